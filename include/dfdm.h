@@ -1,0 +1,195 @@
+/*
+ * dfdm.h -- C ABI of the GB300 fast directional matrix-vector product.
+ *
+ * The library computes g = A v for the Helmholtz matrix of Eq. (1) of
+ * Of & Watschinger, "Complexity Analysis of a Fast Directional
+ * Matrix-Vector Multiplication":
+ *
+ *     A[j,k] = exp(i kappa |x_j - y_k|) / (4 pi |x_j - y_k|),
+ *
+ * x_j in P_T (targets), y_k in P_S (sources), by the fast directional method
+ * of Sect. 2 (Alg. 4) over uniform box cluster trees (Alg. 1), the block
+ * partition of Alg. 2, and the directions of Alg. 3 / Def. 3 / Def. 5.
+ * A coincident (bitwise equal) target/source pair contributes 0, the zero
+ * diagonal of Sect. 4.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a dfdm_status; none aborts or exits.  On an error,
+ *     dfdm_last_error() returns a description (thread-local, never NULL).
+ *   - Points are N x 3 row-major doubles (x0 y0 z0 x1 y1 z1 ...).
+ *   - Complex vectors are interleaved (re, im) pairs: complex128 = 2 doubles
+ *     (precision DFDM_FP64), complex64 = 2 floats (tensor-core precision).
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = the
+ *     legacy default stream).  Device work is ordered on that stream.
+ *   - The caller owns every buffer it passes; the plan owns all device
+ *     tables it creates and frees them in dfdm_plan_destroy.
+ */
+#ifndef DFDM_H
+#define DFDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DFDM_OK = 0,
+  DFDM_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or point      */
+  DFDM_ERR_OOM = 2,         /* device or host allocation failed           */
+  DFDM_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  DFDM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up          */
+  DFDM_ERR_NUMERIC = 5,     /* a scale or value left its representable range */
+  DFDM_ERR_UNSUPPORTED = 6  /* valid input this build does not handle yet  */
+} dfdm_status;
+
+typedef enum {
+  /* Every phase in FP64 on the CUDA cores. */
+  DFDM_FP64 = 0,
+  /* Coupling (M2L) products on the tcgen05 tensor cores with operands split
+   * into two FP16 terms (hi + lo, three products hi*hi + hi*lo + lo*hi) and
+   * FP32 accumulation; the other phases in FP32 with FP64 argument
+   * reduction of kappa |x - y| and of the plane-wave phases. */
+  DFDM_TC_FP16X3 = 1
+} dfdm_precision;
+
+typedef struct {
+  int order;        /* Chebyshev nodes per axis, o = m + 1 (m: degree of Eq. 4); 2..10 */
+  int max_depth;    /* tree depth cap D (Alg. 1 never refines below it); 0..10   */
+  int n_max;        /* Alg. 1 leaf size; 0 = refine every non-empty box to D     */
+  double eta2;      /* eta_2 of (A1), (A3); default 5 (Sect. 4)                  */
+  int l_hf;         /* largest high-frequency level (Eq. 11); -2 = default rule:
+                       largest l with kappa * w_l > 2 (w_l = box side), else -1 */
+  int root_mode;    /* 0: root cube [root_lo, root_lo + root_side]^3;
+                       1: smallest power-of-two cube on a dyadic corner that
+                          holds P_T and P_S                                      */
+  double root_lo[3];
+  double root_side;
+  int precision;    /* dfdm_precision                                            */
+  int nrhs_max;     /* largest nrhs dfdm_apply will be called with (>= 1)        */
+} dfdm_params;
+
+/* Counters of a plan (Table 1 quantities and sizes). */
+typedef struct {
+  int64_t n_targets, n_sources;
+  int32_t depth;            /* p = depth of both trees (uniform)              */
+  int32_t l_hf;             /* largest high-frequency level used              */
+  int64_t n_coupling;       /* N_C: admissible blocks (t,s) in L+, both boxes non-empty */
+  int64_t n_stored_coupling;/* N_SC: distinct (level, box offset) operators   */
+  int64_t n_near_blocks;    /* inadmissible leaf blocks in L-                 */
+  int64_t nf_entries;       /* sum over L- of #t^ * #s^ (nearfield entries)   */
+  int64_t n_leaves_t, n_leaves_s; /* non-empty leaf boxes                     */
+  int64_t device_bytes;     /* device memory held by the plan                 */
+  int32_t level_dirs[16];   /* direction slots per level (|D_used(l)|)        */
+  int64_t level_coupling[16]; /* N_C per level                                */
+  int32_t level_offsets[16];  /* N_SC per level                               */
+} dfdm_stats;
+
+typedef struct dfdm_plan_s *dfdm_plan;
+
+/* Fills *p with the defaults: order 5, max_depth 6, n_max 0, eta2 5,
+ * l_hf -2 (rule), root_mode 0 with the unit cube [0,1]^3, DFDM_FP64,
+ * nrhs_max 1.  Returns DFDM_ERR_INVALID_ARG for p == NULL. */
+dfdm_status dfdm_params_default(dfdm_params *p);
+
+/* Builds both trees (Alg. 1, Morton-keyed, Sect. 2.1), the partition
+ * (Alg. 2 / Def. 2, stored as per-level box-offset tables), the directions
+ * (Alg. 3, Def. 3, Def. 5) and every operator the apply needs (coupling
+ * matrices once per level and offset, 8 reference transfer matrices per
+ * level, directional phase diagonals: Sect. 2.7).
+ *
+ * targets, sources: HOST pointers, n_t x 3 and n_s x 3 doubles; copied.
+ * kappa > 0.  Errors: INVALID_ARG for kappa <= 0 or not finite, n < 1,
+ * non-finite coordinates, points outside the root cube (root_mode 0),
+ * order outside 2..10, max_depth outside 0..10, eta2 <= 0;
+ * UNSUPPORTED when the two trees are not both of uniform depth (all leaves
+ * on one level p; always true for n_max = 0); OOM; CUDA.
+ * On success *out receives the plan; on failure *out is NULL.  The work is
+ * done on `stream`; the call returns after it finished. */
+dfdm_status dfdm_plan_create(const double *targets, int64_t n_t,
+                             const double *sources, int64_t n_s, double kappa,
+                             const dfdm_params *params, void *stream,
+                             dfdm_plan *out);
+
+/* g = A v by Alg. 4 (S2M, M2M, M2L, L2L, L2T, nearfield), for nrhs
+ * right-hand sides.  x: DEVICE pointer, nrhs vectors of n_s complex values
+ * in the caller's source order, vector r at x + r * n_s (complex128 for
+ * DFDM_FP64, complex64 for DFDM_TC_FP16X3).  y: DEVICE pointer, nrhs
+ * vectors of n_t complex values in the caller's target order, overwritten.
+ * 1 <= nrhs <= params.nrhs_max.  Asynchronous on `stream`; no host sync.
+ * Errors: INVALID_ARG (NULL, nrhs), CUDA, NUMERIC (a moment scale left the
+ * FP16 range; reported by the next call of dfdm_plan_check). */
+dfdm_status dfdm_apply(dfdm_plan plan, const void *x, void *y, int nrhs,
+                       void *stream);
+
+/* The same product with HOST buffers: copies x to the device, applies, and
+ * copies y back, all on `stream`; returns after y is on the host. */
+dfdm_status dfdm_apply_host(dfdm_plan plan, const void *x_host, void *y_host,
+                            int nrhs, void *stream);
+
+/* Synchronises `stream` and reports a device-side error flag raised by an
+ * earlier apply (a bounded wait that gave up: TIMEOUT; a scale overflow:
+ * NUMERIC), then clears it. */
+dfdm_status dfdm_plan_check(dfdm_plan plan, void *stream);
+
+/* Copies the plan's counters into *st (host). */
+dfdm_status dfdm_plan_stats(dfdm_plan plan, dfdm_stats *st);
+
+/* Device time of the phases of Alg. 4 in the last dfdm_apply, per right-hand
+ * side summed, from CUDA events recorded on the apply's stream (milliseconds).
+ * m2l_ms[l] is the multiplication phase of level l; launches counts the
+ * library's kernel launches of that apply. */
+typedef struct {
+  double s2m_ms, m2m_ms, split_ms, l2l_ms, l2t_ms, near_ms, total_ms;
+  double m2l_ms[16];
+  int64_t launches;
+} dfdm_timing;
+
+/* Turns per-phase event timing of later applies on (enable != 0) or off.
+ * Timing adds event records to the stream but no synchronisation. */
+dfdm_status dfdm_plan_set_timing(dfdm_plan plan, int enable);
+
+/* Waits for the last timed apply's events and fills *t.  Returns
+ * INVALID_ARG when timing is off or no apply ran since it was turned on. */
+dfdm_status dfdm_plan_timing(dfdm_plan plan, dfdm_timing *t);
+
+/* Exports one level of one tree for bit-exact comparison with Alg. 1:
+ * which = 0 targets, 1 sources; 0 <= level <= depth.  With keys == NULL only
+ * *nboxes is set.  Otherwise keys/begin/end must hold *nboxes entries: the
+ * Morton key of every non-empty box on the level (x in bit 0, Sect. 2.1
+ * child order bx + 2 by + 4 bz), in ascending key order, and its [begin, end)
+ * range in the sorted point order.  perm (n points, may be NULL) receives the
+ * original index of every sorted point: points are sorted by their leaf's
+ * key, and within a leaf by ascending original index (a box above the leaf
+ * level holds the runs of its leaves in key order). */
+dfdm_status dfdm_plan_export_tree(dfdm_plan plan, int which, int level,
+                                  int64_t *nboxes, int64_t *keys,
+                                  int64_t *begin, int64_t *end,
+                                  int64_t *perm);
+
+/* Exports the coupling structure of one level: for target boxes of parity
+ * alpha = (ax, ay, az) (bit i = box coordinate i mod 2), the offsets
+ * d = t - s (integer box units) of all admissible blocks of Alg. 2 whose
+ * parent pair is inadmissible, and the index of c_(l)(t,s) (Def. 3) in
+ * D^(l) for each (0 on low-frequency levels).  alpha_index = ax + 2 ay + 4 az.
+ * With offsets == NULL only *count is set; else offsets holds 3 * *count
+ * int32 and dirs *count int32.  level 0 .. depth. */
+dfdm_status dfdm_plan_export_offsets(dfdm_plan plan, int level,
+                                     int alpha_index, int32_t *count,
+                                     int32_t *offsets, int32_t *dirs);
+
+/* Frees the plan and everything it owns; NULL is allowed. */
+dfdm_status dfdm_plan_destroy(dfdm_plan plan);
+
+/* Description of the last error on this thread (never NULL). */
+const char *dfdm_last_error(void);
+
+/* Library version string (never NULL). */
+const char *dfdm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFDM_H */

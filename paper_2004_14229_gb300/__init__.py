@@ -1,0 +1,258 @@
+"""GB300 fast directional matrix-vector product (Of & Watschinger, Alg. 4).
+
+Thin Python binding of the C ABI in include/dfdm.h: argument marshalling only.
+Every step of the product runs in libdfdm.so's CUDA kernels; there is no CPU
+fallback, and using a plan without the built library raises.  PyTorch is used
+for device memory and streams when the caller passes CUDA tensors.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["DFDMError", "Plan", "load_library", "LIB_PATH", "EXPORTED_SYMBOLS",
+           "FP64", "TC_FP16X3"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdfdm.so")
+
+FP64 = 0
+TC_FP16X3 = 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "NUMERIC",
+          6: "UNSUPPORTED"}
+
+EXPORTED_SYMBOLS = [
+    "dfdm_params_default", "dfdm_plan_create", "dfdm_apply", "dfdm_apply_host",
+    "dfdm_plan_check", "dfdm_plan_stats", "dfdm_plan_export_tree",
+    "dfdm_plan_export_offsets", "dfdm_plan_destroy", "dfdm_last_error", "dfdm_version",
+    "dfdm_plan_set_timing", "dfdm_plan_timing",
+]
+
+
+class DFDMError(RuntimeError):
+    """A dfdm_* call returned a status other than DFDM_OK."""
+
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("max_depth", ctypes.c_int), ("n_max", ctypes.c_int),
+                ("eta2", ctypes.c_double), ("l_hf", ctypes.c_int), ("root_mode", ctypes.c_int),
+                ("root_lo", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+                ("precision", ctypes.c_int), ("nrhs_max", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_targets", ctypes.c_int64), ("n_sources", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("l_hf", ctypes.c_int32),
+                ("n_coupling", ctypes.c_int64), ("n_stored_coupling", ctypes.c_int64),
+                ("n_near_blocks", ctypes.c_int64), ("nf_entries", ctypes.c_int64),
+                ("n_leaves_t", ctypes.c_int64), ("n_leaves_s", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("level_dirs", ctypes.c_int32 * 16),
+                ("level_coupling", ctypes.c_int64 * 16), ("level_offsets", ctypes.c_int32 * 16)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("s2m_ms", ctypes.c_double), ("m2m_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
+                ("l2l_ms", ctypes.c_double), ("l2t_ms", ctypes.c_double), ("near_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("m2l_ms", ctypes.c_double * 16), ("launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libdfdm.so (built by __graft_entry__.build()); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdfdm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "dfdm_params_default": [ctypes.POINTER(Params)],
+        "dfdm_plan_create": [vp, i64, vp, i64, dbl, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)],
+        "dfdm_apply": [vp, vp, vp, i32, vp],
+        "dfdm_apply_host": [vp, vp, vp, i32, vp],
+        "dfdm_plan_check": [vp, vp],
+        "dfdm_plan_stats": [vp, ctypes.POINTER(Stats)],
+        "dfdm_plan_export_tree": [vp, i32, i32, ctypes.POINTER(i64), vp, vp, vp, vp],
+        "dfdm_plan_export_offsets": [vp, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, vp],
+        "dfdm_plan_destroy": [vp],
+        "dfdm_plan_set_timing": [vp, i32],
+        "dfdm_plan_timing": [vp, ctypes.POINTER(Timing)],
+        "dfdm_last_error": [],
+        "dfdm_version": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name in ("dfdm_last_error", "dfdm_version") else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise DFDMError(status, load_library().dfdm_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A plan of the fast directional product for fixed P_T, P_S and kappa.
+
+    targets, sources: (N, 3) float64 arrays (host).  order: Chebyshev nodes per
+    axis (m + 1).  max_depth / n_max: Alg. 1's refinement (n_max = 0 refines
+    every non-empty box to max_depth).  root: (lo[3], side) for an explicit root
+    cube, or "bounding" for the smallest dyadic power-of-two cube.  l_hf: None
+    for the default rule.  precision: FP64 or TC_FP16X3.
+    """
+
+    def __init__(self, targets, sources, kappa, order=5, max_depth=6, n_max=0, eta2=5.0,
+                 l_hf=None, root=((0.0, 0.0, 0.0), 1.0), precision=FP64, nrhs_max=1,
+                 stream=None):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p(0)
+        t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+        s = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+        p = Params()
+        _check(lib.dfdm_params_default(ctypes.byref(p)))
+        p.order, p.max_depth, p.n_max, p.eta2 = int(order), int(max_depth), int(n_max), float(eta2)
+        p.l_hf = -2 if l_hf is None else int(l_hf)
+        if isinstance(root, str) and root == "bounding":
+            p.root_mode = 1
+        else:
+            lo, side = root
+            p.root_mode = 0
+            for i in range(3):
+                p.root_lo[i] = float(lo[i])
+            p.root_side = float(side)
+        p.precision = int(precision)
+        p.nrhs_max = int(nrhs_max)
+        self.precision = int(precision)
+        self.n_targets, self.n_sources = t.shape[0], s.shape[0]
+        self.nrhs_max = int(nrhs_max)
+        _check(lib.dfdm_plan_create(t.ctypes.data, t.shape[0], s.ctypes.data, s.shape[0],
+                                    float(kappa), ctypes.byref(p), _stream_handle(stream),
+                                    ctypes.byref(self._h)))
+
+    # -------------------------------------------------------------- apply
+    @property
+    def complex_dtype(self):
+        return np.complex128 if self.precision == FP64 else np.complex64
+
+    def apply(self, x, y=None, stream=None):
+        """y = A x for CUDA tensors (torch): x of shape (n_s,) or (nrhs, n_s)."""
+        import torch
+        tdt = torch.complex128 if self.precision == FP64 else torch.complex64
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == tdt):
+            raise TypeError("x must be a CUDA tensor of dtype %s" % tdt)
+        x = x.contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        if x.shape[-1] != self.n_sources:
+            raise ValueError("x has %d entries per vector, expected %d" % (x.shape[-1], self.n_sources))
+        shape = (self.n_targets,) if x.dim() == 1 else (nrhs, self.n_targets)
+        if y is None:
+            y = torch.empty(shape, dtype=tdt, device=x.device)
+        _check(self._lib.dfdm_apply(self._h, ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(y.data_ptr()), int(nrhs),
+                                    _stream_handle(stream)))
+        return y
+
+    def apply_host(self, x, y=None, stream=None):
+        """y = A x for host numpy arrays; copies in and out inside the call."""
+        x = np.ascontiguousarray(x, dtype=self.complex_dtype)
+        nrhs = 1 if x.ndim == 1 else x.shape[0]
+        shape = (self.n_targets,) if x.ndim == 1 else (nrhs, self.n_targets)
+        if y is None:
+            y = np.empty(shape, dtype=self.complex_dtype)
+        _check(self._lib.dfdm_apply_host(self._h, x.ctypes.data, y.ctypes.data, int(nrhs),
+                                         _stream_handle(stream)))
+        return y
+
+    def set_timing(self, enable=True):
+        """Record CUDA events around every phase of later applies."""
+        _check(self._lib.dfdm_plan_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self):
+        """Per-phase device milliseconds of the last timed apply (dict)."""
+        t = Timing()
+        _check(self._lib.dfdm_plan_timing(self._h, ctypes.byref(t)))
+        out = {name: (list(getattr(t, name)) if name == "m2l_ms" else getattr(t, name))
+               for name, _ in Timing._fields_}
+        out["launches"] = int(out["launches"])
+        return out
+
+    def check(self, stream=None):
+        _check(self._lib.dfdm_plan_check(self._h, _stream_handle(stream)))
+
+    # ------------------------------------------------------------ queries
+    def stats(self):
+        st = Stats()
+        _check(self._lib.dfdm_plan_stats(self._h, ctypes.byref(st)))
+        out = {}
+        for name, _ in Stats._fields_:
+            v = getattr(st, name)
+            out[name] = list(v) if hasattr(v, "__len__") else int(v)
+        return out
+
+    def export_tree(self, which, level, with_perm=False):
+        """(keys, begin, end[, perm]) of level `level` of the target (0) or source (1) tree."""
+        nb = ctypes.c_int64(0)
+        _check(self._lib.dfdm_plan_export_tree(self._h, int(which), int(level), ctypes.byref(nb),
+                                               None, None, None, None))
+        keys = np.empty(nb.value, dtype=np.int64)
+        begin = np.empty(nb.value, dtype=np.int64)
+        end = np.empty(nb.value, dtype=np.int64)
+        n = self.n_targets if which == 0 else self.n_sources
+        perm = np.empty(n, dtype=np.int64) if with_perm else None
+        _check(self._lib.dfdm_plan_export_tree(
+            self._h, int(which), int(level), ctypes.byref(nb), keys.ctypes.data, begin.ctypes.data,
+            end.ctypes.data, perm.ctypes.data if with_perm else None))
+        return (keys, begin, end, perm) if with_perm else (keys, begin, end)
+
+    def export_offsets(self, level, alpha):
+        """(offsets (k, 3) int32, direction indices (k,)) of Alg. 2's admissible
+        leaves on `level` for targets of parity alpha = ax + 2 ay + 4 az."""
+        cnt = ctypes.c_int32(0)
+        _check(self._lib.dfdm_plan_export_offsets(self._h, int(level), int(alpha),
+                                                  ctypes.byref(cnt), None, None))
+        off = np.empty((cnt.value, 3), dtype=np.int32)
+        dirs = np.empty(cnt.value, dtype=np.int32)
+        _check(self._lib.dfdm_plan_export_offsets(self._h, int(level), int(alpha), ctypes.byref(cnt),
+                                                  off.ctypes.data, dirs.ctypes.data))
+        return off, dirs
+
+    def close(self):
+        if self._h:
+            self._lib.dfdm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,1117 @@
+// Tensor-core form of Alg. 4 (DFDM_TC_FP16X3).
+//
+// M2L, the dense complex contraction g~_t += A~_d v~_{t-d} over all
+// admissible offsets d (Sect. 2.6, multiplication phase), runs on the tcgen05
+// tensor cores:
+//   * complex n x n products are real-stacked: outputs [Re; Im] (rows) times
+//     inputs [Re v; Im v] (K), each padded to NP = KP (a multiple of 32);
+//   * each FP32 operand value a is split into two FP16 terms a = a_hi + a_lo
+//     (a_hi = fp16(a), a_lo = fp16(a - a_hi)) after a power-of-two scale per
+//     level, and the product takes a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32
+//     accumulation in TMEM (the dropped a_lo b_lo is ~2^-22 relative);
+//   * one CTA owns 128 targets of one parity alpha (a 8 x 4 x 4 block of the
+//     parent grid) and walks the level's offset list for alpha; the source
+//     moments of all 128 targets for offset d are one TMA box with element
+//     stride 2 in x, y, z over the dense moment grid, so out-of-grid sources
+//     arrive as zeros;
+//   * the accumulator (128 targets x NP outputs, FP32) lives in TMEM; it is
+//     drained into the FP32 local grid by four epilogue warps every time the
+//     direction slot changes and every kFlushOps offsets, so no FP32 chain in
+//     TMEM grows longer than kFlushOps * 3 * KP / 16 MMA steps.
+// Warp roles: warp 0 issues TMA loads, warp 1 issues MMAs (and owns TMEM),
+// warps 2-5 drain TMEM.  Every wait is bounded; a wait that gives up sets the
+// plan's error word (read by dfdm_plan_check) and the CTA leaves its loop.
+//
+// The other phases (S2M, M2M, L2L, L2T, nearfield) run in FP32 on the CUDA
+// cores with FP64 reduction of large phase arguments; moments and locals are
+// real-stacked FP32 rows [Re 0..n-1 | Im 0..n-1 | pad] of KP floats.
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "sm100_ptx.cuh"
+#include "tc.cuh"
+
+namespace dfdm {
+
+namespace {
+
+// This translation unit's copies of the reference nodes (FP64 and FP32) and
+// barycentric factors; filled by build_tc.
+__constant__ double c_cheb[kMaxOrder];
+__constant__ double c_lagw[kMaxOrder];
+
+constexpr double kPi = 3.14159265358979323846;
+
+__constant__ float c_chebf[kMaxOrder];
+__constant__ float c_lagwf[kMaxOrder];
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// ------------------------------------------------------------ helpers
+template <int O>
+__device__ __forceinline__ void lagrange1f(float t, float *out) {
+#pragma unroll
+  for (int nu = 0; nu < O; ++nu) {
+    float v = c_lagwf[nu];
+#pragma unroll
+    for (int mu = 0; mu < O; ++mu)
+      if (mu != nu) v *= (t - c_chebf[mu]);
+    out[nu] = v;
+  }
+}
+
+// exp(i a) for an FP64 argument: reduced modulo 2 pi in FP64, then FP32.
+__device__ __forceinline__ float2 cexpi_reduced(double a) {
+  const double r = a - 2.0 * kPi * rint(a * (0.5 / kPi));
+  float s, c;
+  sincosf((float)r, &s, &c);
+  return make_float2(c, s);
+}
+
+__device__ __forceinline__ void atomic_max_abs(float *addr, float v) {
+  atomicMax(reinterpret_cast<int *>(addr), __float_as_int(fabsf(v)));
+}
+
+// ------------------------------------------------ operators (FP64 -> FP16x2)
+// Real-stacked coupling operator of (level, d), scaled by 2^e and split:
+// row j < n: [Re A[j, :], -Im A[j, :]]; row NH + j: [Im A[j, :], Re A[j, :]],
+// with NH = NP / 2 the half of the padded output rows.
+__global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t *op_level,
+                                 const int32_t *op_off, const double *op_dir, const double *level_w,
+                                 const float *level_scale, double kappa, __half *ohi, __half *olo) {
+  const int op = blockIdx.y;
+  const int row = blockIdx.x;  // 0 .. 2 NH - 1
+  const int l = op_level[op];
+  const double w = level_w[l], h = 0.5 * w;
+  const float sc = level_scale[l];
+  const bool im_row = row >= NH;
+  const int j = im_row ? row - NH : row;
+  __half *dhi = ohi + ((int64_t)op * 2 * NH + row) * KP;
+  __half *dlo = olo + ((int64_t)op * 2 * NH + row) * KP;
+  const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
+  const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
+  for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
+    float val = 0.0f;
+    const bool kim = kk >= n;
+    const int k = kim ? kk - n : kk;
+    if (j < n && kk < 2 * n) {
+      const int jx = j % order, jy = (j / order) % order, jz = j / (order * order);
+      const int kx = k % order, ky = (k / order) % order, kz = k / (order * order);
+      const double e0 = h * (c_cheb[jx] - c_cheb[kx]);
+      const double e1 = h * (c_cheb[jy] - c_cheb[ky]);
+      const double e2 = h * (c_cheb[jz] - c_cheb[kz]);
+      const double v0 = w * d0 + e0, v1 = w * d1 + e1, v2 = w * d2 + e2;
+      const double r = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      const double arg = kappa * (r - (e0 * c0 + e1 * c1 + e2 * c2));
+      double s, c;
+      sincos(arg, &s, &c);
+      const double inv = 1.0 / (4.0 * kPi * r);
+      const double re = c * inv, im = s * inv;
+      // real-stacked block [[Re, -Im], [Im, Re]]
+      double v;
+      if (!im_row) v = kim ? -im : re;
+      else v = kim ? re : im;
+      val = (float)(v * (double)sc);
+    }
+    const __half hi = __float2half_rn(val);
+    const __half lo = __float2half_rn(val - __half2float(hi));
+    dhi[kk] = hi;
+    dlo[kk] = lo;
+  }
+}
+
+// Centred directional diagonals P_{oct,c}[k] (FP64 arguments) as float2.
+__global__ void k_phase_table_f(int order, int n, int nslots, const double *cvec, const double *c2vec,
+                                double kappa, double h, float2 *tab) {
+  const int oct = blockIdx.y, slot = blockIdx.x;
+  const double b[3] = {(double)(oct & 1), (double)((oct >> 1) & 1), (double)((oct >> 2) & 1)};
+  const double *c = cvec + 3 * slot, *c2 = c2vec + 3 * slot;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int kk[3] = {k % order, (k / order) % order, k / (order * order)};
+    double a = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double r = c_cheb[kk[i]];
+      a += (2.0 * b[i] - 1.0 + r) * c[i] - r * c2[i];
+    }
+    double s, co;
+    sincos(kappa * h * a, &s, &co);
+    tab[((int64_t)oct * nslots + slot) * n + k] = make_float2((float)co, (float)s);
+  }
+}
+
+// Leaf-local FP32 coordinates: x - m_leaf for every sorted point.
+__global__ void k_local_coords(const double *xyz, int64_t n, const int32_t *leaf_cell,
+                               const int32_t *leaf_begin, const int32_t *leaf_end, int64_t nleaves,
+                               double lo0, double lo1, double lo2, double w, int g, float *loc) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nleaves) return;
+  const int cell = leaf_cell[b];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const double m0 = lo0 + (cx + 0.5) * w, m1 = lo1 + (cy + 0.5) * w, m2 = lo2 + (cz + 0.5) * w;
+  for (int p = leaf_begin[b]; p < leaf_end[b]; ++p) {
+    loc[p] = (float)(xyz[p] - m0);
+    loc[n + p] = (float)(xyz[n + p] - m1);
+    loc[2 * n + p] = (float)(xyz[2 * n + p] - m2);
+  }
+}
+
+// ----------------------------------------------------------------- S2M
+template <int O>
+__global__ void __launch_bounds__(128) k_s2m_f32(const float *lxyz, int64_t n_pts, const int32_t *perm,
+                                                 const float2 *x, const int32_t *leaf_cell,
+                                                 const int32_t *leaf_begin, const int32_t *leaf_end,
+                                                 double w, const double *dir, double kappa, float *mom,
+                                                 int64_t ncell, int KP, float *maxabs) {
+  constexpr int N = O * O * O;
+  constexpr int CH = 32;
+  constexpr int PER = (N + 127) / 128;
+  __shared__ float sl[3][CH][O];
+  __shared__ float2 sq[CH];
+  const int leaf = blockIdx.x, slot = blockIdx.y;
+  const int cell = leaf_cell[leaf];
+  const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
+  const float inv_h = (float)(2.0 / w);
+  float2 acc[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc[i] = make_float2(0.f, 0.f);
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  for (int p0 = b; p0 < e; p0 += CH) {
+    const int cnt = min(CH, e - p0);
+    if (threadIdx.x < cnt) {
+      const int p = p0 + threadIdx.x;
+      const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
+      lagrange1f<O>(y0 * inv_h, sl[0][threadIdx.x]);
+      lagrange1f<O>(y1 * inv_h, sl[1][threadIdx.x]);
+      lagrange1f<O>(y2 * inv_h, sl[2][threadIdx.x]);
+      const float2 ph = cexpi_reduced(-kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
+      const float2 v = x[perm[p]];
+      sq[threadIdx.x] = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int k = threadIdx.x + 128 * i;
+      if (k < N) {
+        const int kx = k % O, ky = (k / O) % O, kz = k / (O * O);
+        for (int q = 0; q < cnt; ++q) {
+          const float l = sl[0][q][kx] * sl[1][q][ky] * sl[2][q][kz];
+          acc[i].x = fmaf(l, sq[q].x, acc[i].x);
+          acc[i].y = fmaf(l, sq[q].y, acc[i].y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  float mx = 0.f;
+  float *dst = mom + ((int64_t)slot * ncell + cell) * KP;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int k = threadIdx.x + 128 * i;
+    if (k < N) {
+      dst[k] = acc[i].x;
+      dst[N + k] = acc[i].y;
+      mx = fmaxf(mx, fmaxf(fabsf(acc[i].x), fabsf(acc[i].y)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomic_max_abs(maxabs, mx);
+}
+
+// ------------------------------------------------------ M2M / L2L (FP32)
+// Apply E_oct^T (M2M) or E_oct (L2L) axis by axis to the complex smem vector
+// (ur, ui) of N = O^3 entries; e1[b][k][l] = L_l((2b - 1 + r_k) / 2).
+template <int O>
+__device__ void tensor_transfer_f(const float *e1, int oct, bool transpose, float *ur, float *ui, float *tr,
+                                  float *ti) {
+  constexpr int N = O * O * O;
+  const int b[3] = {oct & 1, (oct >> 1) & 1, (oct >> 2) & 1};
+  for (int a = 0; a < 3; ++a) {
+    const int stride = (a == 0) ? 1 : (a == 1 ? O : O * O);
+    const float *m = e1 + b[a] * O * O;
+    for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+      const int i = (idx / stride) % O;
+      const int base = idx - i * stride;
+      float sr = 0.f, si = 0.f;
+#pragma unroll
+      for (int q = 0; q < O; ++q) {
+        const float e = transpose ? m[q * O + i] : m[i * O + q];
+        sr = fmaf(e, ur[base + q * stride], sr);
+        si = fmaf(e, ui[base + q * stride], si);
+      }
+      tr[idx] = sr;
+      ti[idx] = si;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+      ur[idx] = tr[idx];
+      ui[idx] = ti[idx];
+    }
+    __syncthreads();
+  }
+}
+
+template <int O>
+__global__ void __launch_bounds__(128) k_m2m_f32(const float *cmom, float *pmom, int gp,
+                                                 const int32_t *child_slot, const float2 *phase, int nslot_p,
+                                                 const float *e1, int KP, float *maxabs) {
+  constexpr int N = O * O * O;
+  constexpr int PER = (N + 127) / 128;
+  __shared__ float ur[N], ui[N], tr[N], ti[N];
+  __shared__ float se1[2 * O * O];
+  const int64_t cellp = blockIdx.x;
+  const int slot = blockIdx.y;
+  const int cs = child_slot[slot];
+  const int64_t gc = 2 * (int64_t)gp;
+  const int64_t ncp = (int64_t)gp * gp * gp, ncc = gc * gc * gc;
+  const int x = cellp % gp, y = (cellp / gp) % gp, z = cellp / ((int64_t)gp * gp);
+  for (int i = threadIdx.x; i < 2 * O * O; i += blockDim.x) se1[i] = e1[i];
+  float ar[PER], ai[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) ar[i] = ai[i] = 0.f;
+  __syncthreads();
+  for (int oct = 0; oct < 8; ++oct) {
+    const int64_t cc = (2 * x + (oct & 1)) + gc * ((2 * y + ((oct >> 1) & 1)) + gc * (2 * z + (oct >> 2)));
+    const float *src = cmom + ((int64_t)cs * ncc + cc) * KP;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      float vr = src[k], vi = src[N + k];
+      if (phase) {  // times conj(P)
+        const float2 p = phase[((int64_t)oct * nslot_p + slot) * N + k];
+        const float r = vr * p.x + vi * p.y;
+        vi = vi * p.x - vr * p.y;
+        vr = r;
+      }
+      ur[k] = vr;
+      ui[k] = vi;
+    }
+    __syncthreads();
+    tensor_transfer_f<O>(se1, oct, true, ur, ui, tr, ti);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int k = threadIdx.x + 128 * i;
+      if (k < N) {
+        ar[i] += ur[k];
+        ai[i] += ui[k];
+      }
+    }
+    __syncthreads();
+  }
+  float mx = 0.f;
+  float *dst = pmom + ((int64_t)slot * ncp + cellp) * KP;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int k = threadIdx.x + 128 * i;
+    if (k < N) {
+      dst[k] = ar[i];
+      dst[N + k] = ai[i];
+      mx = fmaxf(mx, fmaxf(fabsf(ar[i]), fabsf(ai[i])));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomic_max_abs(maxabs, mx);
+}
+
+template <int O>
+__global__ void __launch_bounds__(128) k_l2l_f32(const float *ploc, float *cloc, int gc, const int32_t *pslots,
+                                                 const int32_t *pslot_off, const float2 *phase, int nslot_p,
+                                                 const float *e1, int KP) {
+  constexpr int N = O * O * O;
+  constexpr int PER = (N + 127) / 128;
+  __shared__ float ur[N], ui[N], tr[N], ti[N];
+  __shared__ float se1[2 * O * O];
+  const int64_t cellc = blockIdx.x;
+  const int cs = blockIdx.y;
+  const int gp = gc / 2;
+  const int64_t ncp = (int64_t)gp * gp * gp, ncc = (int64_t)gc * gc * gc;
+  const int x = cellc % gc, y = (cellc / gc) % gc, z = cellc / ((int64_t)gc * gc);
+  const int oct = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+  const int64_t cellp = (x >> 1) + (int64_t)gp * ((y >> 1) + (int64_t)gp * (z >> 1));
+  for (int i = threadIdx.x; i < 2 * O * O; i += blockDim.x) se1[i] = e1[i];
+  float ar[PER], ai[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) ar[i] = ai[i] = 0.f;
+  __syncthreads();
+  for (int q = pslot_off[cs]; q < pslot_off[cs + 1]; ++q) {
+    const int ps = pslots[q];
+    const float *src = ploc + ((int64_t)ps * ncp + cellp) * KP;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      ur[k] = src[k];
+      ui[k] = src[N + k];
+    }
+    __syncthreads();
+    tensor_transfer_f<O>(se1, oct, false, ur, ui, tr, ti);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int k = threadIdx.x + 128 * i;
+      if (k < N) {
+        float vr = ur[k], vi = ui[k];
+        if (phase) {
+          const float2 p = phase[((int64_t)oct * nslot_p + ps) * N + k];
+          const float r = vr * p.x - vi * p.y;
+          vi = vr * p.y + vi * p.x;
+          vr = r;
+        }
+        ar[i] += vr;
+        ai[i] += vi;
+      }
+    }
+    __syncthreads();
+  }
+  float *dst = cloc + ((int64_t)cs * ncc + cellc) * KP;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int k = threadIdx.x + 128 * i;
+    if (k < N) {
+      dst[k] += ar[i];
+      dst[N + k] += ai[i];
+    }
+  }
+}
+
+// ------------------------------------------------ FP32 -> FP16 hi/lo split
+__global__ void k_split(const float *src, int64_t count, const float *maxabs, int *exp_out, __half *hi,
+                        __half *lo) {
+  // scale 2^e with max * 2^e <= 2^14
+  const float mx = *maxabs;
+  int e = 0;
+  if (mx > 0.f) e = 14 - (int)ceilf(log2f(mx));
+  if (e > 60) e = 60;
+  if (e < -60) e = -60;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = e;
+  const float sc = ldexpf(1.0f, e);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = src[i] * sc;
+    const __half h = __float2half_rn(v);
+    hi[i] = h;
+    lo[i] = __float2half_rn(v - __half2float(h));
+  }
+}
+
+// ------------------------------------------------------------- M2L (TC)
+// One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
+// grid), all NP stacked outputs, one level.  Per K step of 16:
+//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi
+//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo
+// so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 hold the cross
+// terms X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one smem
+// buffer [Z | M_hi | M_lo]).  The tensor core truncates its FP32
+// accumulator towards zero after every instruction, so H is drained into an
+// FP32 shared-memory sum R (round to nearest) after every operator: no H
+// chain is longer than KP / 16 instructions.  X is 2^-11 of H and is drained
+// into R every kFlushOps operators; R goes to the FP32 local grid at the
+// same points and when the direction slot changes.
+struct M2lArgs {
+  const int32_t *alpha_ops;   // level's op list (global op indices), per alpha
+  const int32_t *alpha_off;   // 9 offsets into alpha_ops
+  const int32_t *op_off;      // 3 ints per global op
+  const int32_t *op_slot;     // slot per global op
+  int op_base;                // first global op of the level
+  float *loc;                 // FP32 locals [slot][cell][KP]
+  int g;                      // level grid
+  int n;                      // nodes per box
+  int KP;                     // padded stacked length (= NP)
+  const int *mom_exp;         // moment scale exponent of the level (device)
+  int op_exp;                 // operator scale exponent of the level
+  int *err;                   // error word
+};
+
+constexpr int kTM = 64;                   // targets per CTA
+constexpr int kTX = 4, kTY = 4, kTZ = 4;  // parent-grid block of a CTA
+constexpr int kK = 16;                    // K per stage (32-byte rows)
+constexpr int kSt = 3;                    // pipeline stages
+constexpr int kM2lWarps = 18;             // 0 TMA, 1 MMA, 2-3 X drain, 4.. H drain
+constexpr int kM2lThreads = kM2lWarps * 32;
+constexpr int kEpiThreads = 10 * 32;      // warps 2, 3 and the eight H warps
+constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int kFlushOps = 32;
+
+template <int NP>
+struct M2lSmem {
+  static constexpr int kRowB = kK * 2;                 // bytes per operand row
+  static constexpr int kZ = kTM * kRowB;               // zero rows
+  static constexpr int kM = kTM * kRowB;               // 64 moment rows
+  static constexpr int kO = NP * kRowB;                // operator rows
+  static constexpr int kOffMhi = kZ, kOffMlo = kZ + kM, kOffOhi = kZ + 2 * kM, kOffOlo = kZ + 2 * kM + kO;
+  static constexpr int kStage = kZ + 2 * kM + 2 * kO;
+  static constexpr int kR = kTM * NP * 4;              // FP32 running sums R[col][row]
+  static constexpr int kTotal = kSt * kStage + kR + 1024;
+  static_assert(kStage % 1024 == 0, "stage alignment");
+};
+
+// Epilogue warp roles: H warps are quarters 0 / 1 (lanes 0..63), four column
+// groups each; X warps 2 and 3 are quarters 2 / 3 (lanes 64..127).
+__device__ __forceinline__ int h_group(int warp) { return (warp >= 4 && warp < 20 && (warp & 3) < 2) ? (warp - 4) / 4 : -1; }
+
+template <int NP>
+__global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant__ CUtensorMap map_mhi,
+                                                          const __grid_constant__ CUtensorMap map_mlo,
+                                                          const __grid_constant__ CUtensorMap map_ohi,
+                                                          const __grid_constant__ CUtensorMap map_olo,
+                                                          const M2lArgs args) {
+  using S = M2lSmem<NP>;
+  constexpr int NH = NP / 2;          // N of one MMA (<= 256)
+  constexpr int KSTEPS = NP / kK;     // stages per operator (KP == NP)
+  constexpr int GCOLS = NP / 4;       // columns per H warp
+  constexpr uint32_t kTmemCols = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
+  static_assert(NH % 16 == 0 && NH <= 256, "N half must be a multiple of 16, <= 256");
+  static_assert(GCOLS % 16 == 0, "H warp column group must be a multiple of 16");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NP][kTM]
+  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full, acc_empty;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = args.g, gp = g >> 1;
+  const int tiles_x = (gp + kTX - 1) / kTX, tiles_y = (gp + kTY - 1) / kTY;
+  const int alpha = blockIdx.y;
+  const int tile = blockIdx.x;
+  const int X0 = (tile % tiles_x) * kTX;
+  const int Y0 = ((tile / tiles_x) % tiles_y) * kTY;
+  const int Z0 = (tile / (tiles_x * tiles_y)) * kTZ;
+  const int ax = alpha & 1, ay = (alpha >> 1) & 1, az = (alpha >> 2) & 1;
+  const int i0 = args.alpha_off[alpha], i1 = args.alpha_off[alpha + 1];
+
+  // zero rows of every stage and the running sums
+  for (int s = 0; s < kSt; ++s)
+    for (int i = tid; i < S::kZ / 16; i += blockDim.x)
+      reinterpret_cast<uint4 *>(smem + s * S::kStage)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < kTM * NP; i += blockDim.x) R[i] = 0.f;
+  ptx::fence_proxy_async();
+  if (tid == 0) {
+    for (int s = 0; s < kSt; ++s) {
+      ptx::mbar_init(&full_bar[s], 1);
+      ptx::mbar_init(&empty_bar[s], 1);
+    }
+    ptx::mbar_init(&acc_full, 1);
+    ptx::mbar_init(&acc_empty, kEpiThreads / 32);
+    s_abort = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(&tmem_base, kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      ptx::prefetch_tensormap(&map_mhi);
+      ptx::prefetch_tensormap(&map_mlo);
+      ptx::prefetch_tensormap(&map_ohi);
+      ptx::prefetch_tensormap(&map_olo);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int ii = i0; ii < i1 && ok; ++ii) {
+        const int op = args.alpha_ops[ii];
+        const int slot = args.op_slot[op];
+        const int x0 = 2 * X0 + ax - args.op_off[3 * op];
+        const int y0 = 2 * Y0 + ay - args.op_off[3 * op + 1];
+        const int z0 = 2 * Z0 + az - args.op_off[3 * op + 2];
+        const int opl = op - args.op_base;
+        for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
+          const int st = it % kSt;
+          const uint32_t ph = (it / kSt) & 1;
+          if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
+          uint8_t *base = smem + st * S::kStage;
+          ptx::mbar_expect_tx(&full_bar[st], 2 * S::kM + 2 * S::kO);
+          ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
+          ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
+          ptx::tma_load_3d(base + S::kOffOhi, &map_ohi, &full_bar[st], kc * kK, 0, opl);
+          ptx::tma_load_3d(base + S::kOffOhi + S::kO / 2, &map_ohi, &full_bar[st], kc * kK, NH, opl);
+          ptx::tma_load_3d(base + S::kOffOlo, &map_olo, &full_bar[st], kc * kK, 0, opl);
+          ptx::tma_load_3d(base + S::kOffOlo + S::kO / 2, &map_olo, &full_bar[st], kc * kK, NH, opl);
+        }
+      }
+      if (!ok) {
+        atomicExch(args.err, 1);
+        atomicExch(&s_abort, 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = ptx::idesc_f16_f32(128, NH);
+      uint32_t it = 0;
+      bool first = true, ok = true;
+      int j = 0;
+      for (int ii = i0; ii < i1 && ok; ++ii, ++j) {
+        for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
+          const int st = it % kSt;
+          const uint32_t ph = (it / kSt) & 1;
+          if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
+          const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
+          const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d = tmem + h * NH;
+            ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi + h * (S::kO / 2)), idesc, first ? 0u : 1u);
+            ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo + h * (S::kO / 2)), idesc, 1u);
+          }
+          first = false;
+          ptx::mma_commit(&empty_bar[st]);
+        }
+        if (!ok) break;
+        ptx::mma_commit(&acc_full);
+        if (!ptx::mbar_wait(&acc_empty, j & 1, kWaitLimit)) { ok = false; break; }
+        ptx::tc_fence_after();
+      }
+      if (!ok) {
+        atomicExch(args.err, 1);
+        atomicExch(&s_abort, 1);
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue
+    const int hg = h_group(warp);
+    const bool xw = (warp == 2 || warp == 3);
+    if (hg >= 0 || xw) {
+      const int q = warp & 3;                        // TMEM lane quarter
+      const int r = (q & 1) * 32 + lane;             // target row 0..63
+      const int ix = r % kTX, iy = (r / kTX) % kTY, iz = r / (kTX * kTY);
+      const int X = X0 + ix, Y = Y0 + iy, Z = Z0 + iz;
+      const bool valid = X < gp && Y < gp && Z < gp;
+      const int64_t cell = (2 * X + ax) + (int64_t)g * ((2 * Y + ay) + (int64_t)g * (2 * Z + az));
+      const int64_t ncell = (int64_t)g * g * g;
+      const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
+      const int n = args.n;
+      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+      int run = 0;
+      int j = 0;
+      for (int ii = i0; ii < i1; ++ii, ++j) {
+        const int slot = args.op_slot[args.alpha_ops[ii]];
+        const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
+        ++run;
+        const bool group_end = (next_slot != slot) || run >= kFlushOps;
+        // wait for the operator's MMAs; every epilogue warp then meets at a
+        // named barrier, so a give-up is seen by all of them at the same op
+        bool got = false;
+        {
+          const uint64_t t0 = ptx::global_ns();
+          for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
+            got = ptx::mbar_try_wait(&acc_full, j & 1);
+            if (!got && (t & 255) == 255 &&
+                (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
+              break;
+          }
+        }
+        if (!got) atomicExch(args.err, 1);
+        const bool stop = !got || *(volatile int *)&s_abort;
+        if (ptx::named_bar_or(2, kEpiThreads, stop)) break;   // same decision in every epilogue warp
+        ptx::tc_fence_after();
+        if (hg >= 0) {
+          // H -> R (round to nearest), then clear H
+          const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+          for (int c = hg * GCOLS; c < (hg + 1) * GCOLS; c += 16) {
+            float v[16];
+            ptx::tmem_ld16(tmem + lane_addr + c, v);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
+            ptx::tmem_st16(tmem + lane_addr + c, zero);
+          }
+          ptx::tmem_st_wait();
+        }
+        if (group_end) {
+          ptx::named_bar(1, kEpiThreads);
+          if (xw) {
+            // X -> R, then clear X
+            const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int c = 0; c < NP; c += 16) {
+              float v[16];
+              ptx::tmem_ld16(tmem + lane_addr + c, v);
+              ptx::tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
+              ptx::tmem_st16(tmem + lane_addr + c, zero);
+            }
+            ptx::tmem_st_wait();
+          }
+          ptx::named_bar(1, kEpiThreads);
+          if (hg >= 0) {
+            // R -> local grid (scaled), then clear R
+            float *dst = args.loc + ((int64_t)slot * ncell + cell) * args.KP;
+#pragma unroll 1
+            for (int c = hg * GCOLS; c < (hg + 1) * GCOLS; ++c) {
+              const int jj = (c < NH) ? c : c - NH;
+              const float val = R[c * kTM + r];
+              R[c * kTM + r] = 0.f;
+              if (valid && jj < n) dst[(c < NH) ? jj : n + jj] += val * inv;
+            }
+          }
+          run = 0;
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&acc_empty);
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) ptx::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ----------------------------------------------------------------- L2T
+template <int O>
+__global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
+                                                 const int32_t *leaf_begin, const int32_t *leaf_end, double w,
+                                                 const double *dir, int nslots, double kappa, const float *loc,
+                                                 int64_t ncell, int KP, float2 *ysorted) {
+  constexpr int N = O * O * O;
+  __shared__ float2 red[4];
+  const int leaf = blockIdx.x;
+  const int cell = leaf_cell[leaf];
+  const float inv_h = (float)(2.0 / w);
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  for (int p = b; p < e; ++p) {
+    const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
+    float lx[O], ly[O], lz[O];
+    lagrange1f<O>(y0 * inv_h, lx);
+    lagrange1f<O>(y1 * inv_h, ly);
+    lagrange1f<O>(y2 * inv_h, lz);
+    float2 tot = make_float2(0.f, 0.f);
+    for (int slot = 0; slot < nslots; ++slot) {
+      const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
+      float sr = 0.f, si = 0.f;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int kx = k % O, ky = (k / O) % O, kz = k / (O * O);
+        const float l = lx[kx] * ly[ky] * lz[kz];
+        sr = fmaf(l, src[k], sr);
+        si = fmaf(l, src[N + k], si);
+      }
+      const float2 ph = cexpi_reduced(kappa * ((double)y0 * dir[3 * slot] + (double)y1 * dir[3 * slot + 1] +
+                                               (double)y2 * dir[3 * slot + 2]));
+      tot.x += sr * ph.x - si * ph.y;
+      tot.y += sr * ph.y + si * ph.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      tot.x += __shfl_down_sync(0xffffffffu, tot.x, o);
+      tot.y += __shfl_down_sync(0xffffffffu, tot.y, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float2 r = red[0];
+      for (int i = 1; i < 4; ++i) {
+        r.x += red[i].x;
+        r.y += red[i].y;
+      }
+      ysorted[p] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------- nearfield (FP32)
+// One block per target leaf; source points of each nearfield leaf staged in
+// shared memory; leaf-local coordinates keep |x - y| accurate in FP32
+// (m_t - m_s = w d is exact).
+__global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
+                                                 const int32_t *leaf_cell, const int32_t *leaf_begin,
+                                                 const int32_t *leaf_end, const float *sl, int64_t ns,
+                                                 const int32_t *sperm, const int32_t *s_leaf_of_cell,
+                                                 const int32_t *sb, const int32_t *se, int g, float w,
+                                                 const int32_t *near_off, int nnear, float kappa,
+                                                 const float2 *x, const float2 *ysorted, float2 *y) {
+  __shared__ float4 sp[128];   // x, y, z (local, shifted), unused
+  __shared__ float2 sv[128];
+  const int leaf = blockIdx.x;
+  const int cell = leaf_cell[leaf];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  for (int p0 = b; p0 < e; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const bool act = p < e;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
+    if (act) {
+      x0 = tl[p];
+      x1 = tl[nt + p];
+      x2 = tl[2 * nt + p];
+      acc = ysorted[p];
+    }
+    for (int i = 0; i < nnear; ++i) {
+      const int dx = near_off[3 * i], dy = near_off[3 * i + 1], dz = near_off[3 * i + 2];
+      const int sx = cx - dx, sy = cy - dy, sz = cz - dz;
+      if (sx < 0 || sy < 0 || sz < 0 || sx >= g || sy >= g || sz >= g) continue;
+      const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
+      if (s < 0) continue;
+      const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
+      for (int q0 = sb[s]; q0 < se[s]; q0 += 128) {
+        const int cnt = min(128, se[s] - q0);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+          const int q = q0 + threadIdx.x;
+          // source position relative to the target leaf's centre
+          sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
+          sv[threadIdx.x] = x[sperm[q]];
+        }
+        __syncthreads();
+        if (act) {
+          for (int k = 0; k < cnt; ++k) {
+            const float d0 = x0 - sp[k].x, d1 = x1 - sp[k].y, d2 = x2 - sp[k].z;
+            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            if (r2 == 0.f) continue;   // coincident points (zero diagonal)
+            const float ir = rsqrtf(r2);
+            const float r = r2 * ir;
+            float s, c;
+            sincosf(kappa * r, &s, &c);
+            const float sc = inv4pi * ir;
+            const float2 v = sv[k];
+            acc.x = fmaf(sc, c * v.x - s * v.y, acc.x);
+            acc.y = fmaf(sc, c * v.y + s * v.x, acc.y);
+          }
+        }
+      }
+    }
+    if (act) y[tperm[p]] = acc;
+  }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    DFDM_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (!p || q != cudaDriverEntryPointSuccess)
+      throw Error{DFDM_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+void encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *ptr, const cuuint64_t *dims,
+            const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *es, CUtensorMapSwizzle sw) {
+  CUresult r = tensor_map_encoder()(m, dt, rank, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{DFDM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
+}
+
+}  // namespace
+
+// Per-plan state of the tensor-core form.
+struct TcState {
+  int KP = 0;                            // = NP, padded stacked length
+  std::vector<float *> mom32, loc32;     // per level FP32 grids
+  std::vector<__half *> mhi, mlo;        // per level split moments
+  std::vector<CUtensorMap> map_mhi, map_mlo, map_ohi, map_olo;
+  __half *ohi = nullptr, *olo = nullptr; // split operators [op][NP][KP]
+  std::vector<int> op_exp;               // per level operator scale exponent
+  float *maxabs = nullptr;               // per level max |moment|
+  int *mom_exp = nullptr;                // per level moment exponent
+  float *e1 = nullptr;                   // FP32 1-D transfer matrices
+  float2 *phase = nullptr;               // FP32 directional diagonals
+  float *tl = nullptr, *sl = nullptr;    // leaf-local coordinates
+  float2 *ysorted = nullptr;
+};
+
+static TcState &tc_state(Plan &plan) {
+  if (!plan.tc) plan.tc = new TcState();
+  return *plan.tc;
+}
+
+void destroy_tc(Plan &plan) {
+  delete plan.tc;
+  plan.tc = nullptr;
+}
+
+void build_tc(Plan &plan, cudaStream_t st) {
+  TcState &T = tc_state(plan);
+  const int o = plan.order, n = plan.n, p = plan.depth;
+  if (o > 7) throw Error{DFDM_ERR_UNSUPPORTED, "tensor-core form supports orders 2..7"};
+  const int KP = round_up(2 * n, 64);  // stacked length: N halves and H-drain groups of 16
+  if (KP / 2 > 256) throw Error{DFDM_ERR_UNSUPPORTED, "order too large for one MMA N half"};
+  T.KP = KP;
+  // FP32 constants
+  {
+    double cheb[kMaxOrder] = {0}, lagw[kMaxOrder] = {0};
+    chebyshev_tables(o, cheb, lagw);
+    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_cheb, cheb, sizeof(cheb)));
+    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_lagw, lagw, sizeof(lagw)));
+    float cf[kMaxOrder], lf[kMaxOrder];
+    for (int i = 0; i < kMaxOrder; ++i) {
+      cf[i] = (float)cheb[i];
+      lf[i] = (float)lagw[i];
+    }
+    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_chebf, cf, sizeof(cf)));
+    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_lagwf, lf, sizeof(lf)));
+    std::vector<double> e1d(2 * o * o);
+    DFDM_CUDA_TRY(cudaMemcpy(e1d.data(), plan.e1, e1d.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<float> e1f(e1d.begin(), e1d.end());
+    T.e1 = plan.alloc<float>(e1f.size());
+    DFDM_CUDA_TRY(cudaMemcpy(T.e1, e1f.data(), e1f.size() * 4, cudaMemcpyHostToDevice));
+  }
+  // directional diagonals in FP32 (FP64 arguments)
+  if (plan.m2m_phase) {
+    int64_t total = 0;
+    for (int l = 0; l < p; ++l)
+      if (plan.m2m_phase_off[l] >= 0) total = std::max<int64_t>(total, plan.m2m_phase_off[l] + 8ll * plan.levels[l].slot_dir.size() * n);
+    T.phase = plan.alloc<float2>(total);
+    for (int l = plan.min_level; l < p; ++l) {
+      if (plan.m2m_phase_off[l] < 0) continue;
+      const LevelPlan &L = plan.levels[l];
+      const LevelPlan &C = plan.levels[l + 1];
+      const int ns = (int)L.slot_dir.size();
+      std::vector<double> c2(3 * ns);
+      for (int s = 0; s < ns; ++s)
+        for (int i = 0; i < 3; ++i) c2[3 * s + i] = C.dir_vec[3 * L.child_slot[s] + i];
+      double *d_c = nullptr, *d_c2 = nullptr;
+      DFDM_CUDA_TRY(cudaMalloc(&d_c, 3 * ns * 8));
+      DFDM_CUDA_TRY(cudaMalloc(&d_c2, 3 * ns * 8));
+      DFDM_CUDA_TRY(cudaMemcpy(d_c, L.dir_vec.data(), 3 * ns * 8, cudaMemcpyHostToDevice));
+      DFDM_CUDA_TRY(cudaMemcpy(d_c2, c2.data(), 3 * ns * 8, cudaMemcpyHostToDevice));
+      k_phase_table_f<<<dim3(ns, 8), 128, 0, st>>>(o, n, ns, d_c, d_c2, plan.kappa, 0.25 * L.w,
+                                                   T.phase + plan.m2m_phase_off[l]);
+      DFDM_LAUNCH_CHECK();
+      DFDM_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(d_c);
+      cudaFree(d_c2);
+    }
+  }
+  // leaf-local coordinates
+  T.tl = plan.alloc<float>(3 * plan.tt.n);
+  T.sl = plan.alloc<float>(3 * plan.ts.n);
+  const double wl = plan.levels[p].w;
+  k_local_coords<<<nblk(plan.tt.nleaves, 128), 128, 0, st>>>(plan.tt.xyz, plan.tt.n, plan.tt.leaf_cell,
+                                                             plan.tt.leaf_begin, plan.tt.leaf_end, plan.tt.nleaves,
+                                                             plan.root_lo[0], plan.root_lo[1], plan.root_lo[2], wl,
+                                                             1 << p, T.tl);
+  DFDM_LAUNCH_CHECK();
+  k_local_coords<<<nblk(plan.ts.nleaves, 128), 128, 0, st>>>(plan.ts.xyz, plan.ts.n, plan.ts.leaf_cell,
+                                                             plan.ts.leaf_begin, plan.ts.leaf_end, plan.ts.nleaves,
+                                                             plan.root_lo[0], plan.root_lo[1], plan.root_lo[2], wl,
+                                                             1 << p, T.sl);
+  DFDM_LAUNCH_CHECK();
+  T.ysorted = plan.alloc<float2>(plan.tt.n);
+  // grids
+  T.mom32.assign(p + 1, nullptr);
+  T.loc32.assign(p + 1, nullptr);
+  T.mhi.assign(p + 1, nullptr);
+  T.mlo.assign(p + 1, nullptr);
+  T.map_mhi.resize(p + 1);
+  T.map_mlo.resize(p + 1);
+  T.map_ohi.resize(p + 1);
+  T.map_olo.resize(p + 1);
+  T.op_exp.assign(p + 1, 0);
+  T.maxabs = plan.alloc<float>(p + 1);
+  T.mom_exp = plan.alloc<int>(p + 1);
+  DFDM_CUDA_TRY(cudaMemset(T.mom_exp, 0, (p + 1) * sizeof(int)));
+  for (int l = plan.min_level; l <= p; ++l) {
+    const size_t cnt = plan.levels[l].slot_dir.size() * ((size_t)1 << (3 * l)) * KP;
+    T.mom32[l] = plan.alloc<float>(cnt);
+    T.loc32[l] = plan.alloc<float>(cnt);
+    if (!plan.levels[l].off.empty()) {
+      T.mhi[l] = plan.alloc<__half>(cnt);
+      T.mlo[l] = plan.alloc<__half>(cnt);
+      const int gl = 1 << l;
+      const cuuint64_t dims[5] = {(cuuint64_t)KP, (cuuint64_t)gl, (cuuint64_t)gl, (cuuint64_t)gl,
+                                  (cuuint64_t)plan.levels[l].slot_dir.size()};
+      const cuuint64_t strides[4] = {(cuuint64_t)KP * 2, (cuuint64_t)KP * 2 * gl, (cuuint64_t)KP * 2 * gl * gl,
+                                     (cuuint64_t)KP * 2 * gl * gl * gl};
+      const cuuint32_t box[5] = {(cuuint32_t)kK, 2 * kTX, 2 * kTY, 2 * kTZ, 1};
+      const cuuint32_t es[5] = {1, 2, 2, 2, 1};
+      encode(&T.map_mhi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mhi[l], dims, strides, box, es,
+             CU_TENSOR_MAP_SWIZZLE_32B);
+      encode(&T.map_mlo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mlo[l], dims, strides, box, es,
+             CU_TENSOR_MAP_SWIZZLE_32B);
+    }
+  }
+  // split operators, one scale per level: |A~| <= 1 / (4 pi w (2 - r_max))
+  const int nops = plan.n_ops;
+  if (nops > 0) {
+    std::vector<int32_t> op_level;
+    std::vector<double> op_dir, level_w;
+    std::vector<float> level_scale(p + 1, 1.0f);
+    const double rmax = std::cos(kPi / (2.0 * o));
+    for (auto &L : plan.levels) {
+      level_w.push_back(L.w);
+      const double amax = 1.0 / (4.0 * kPi * L.w * (2.0 - rmax));
+      const int e = 14 - (int)std::ceil(std::log2(amax));
+      T.op_exp[L.level] = e;
+      level_scale[L.level] = std::ldexp(1.0f, e);
+      for (size_t i = 0; i < L.op_dir.size(); ++i) {
+        op_level.push_back(L.level);
+        double c[3];
+        direction_vector(plan.l_hf, L.level, L.op_dir[i], c);
+        op_dir.insert(op_dir.end(), c, c + 3);
+      }
+    }
+    int32_t *d_level = nullptr;
+    double *d_dir = nullptr, *d_w = nullptr;
+    float *d_sc = nullptr;
+    DFDM_CUDA_TRY(cudaMalloc(&d_level, nops * 4));
+    DFDM_CUDA_TRY(cudaMalloc(&d_dir, nops * 3 * 8));
+    DFDM_CUDA_TRY(cudaMalloc(&d_w, level_w.size() * 8));
+    DFDM_CUDA_TRY(cudaMalloc(&d_sc, level_scale.size() * 4));
+    DFDM_CUDA_TRY(cudaMemcpy(d_level, op_level.data(), nops * 4, cudaMemcpyHostToDevice));
+    DFDM_CUDA_TRY(cudaMemcpy(d_dir, op_dir.data(), nops * 3 * 8, cudaMemcpyHostToDevice));
+    DFDM_CUDA_TRY(cudaMemcpy(d_w, level_w.data(), level_w.size() * 8, cudaMemcpyHostToDevice));
+    DFDM_CUDA_TRY(cudaMemcpy(d_sc, level_scale.data(), level_scale.size() * 4, cudaMemcpyHostToDevice));
+    const size_t ocnt = (size_t)nops * KP * KP;
+    T.ohi = plan.alloc<__half>(ocnt);
+    T.olo = plan.alloc<__half>(ocnt);
+    k_coupling_split<<<dim3(KP, nops), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
+                                                      d_sc, plan.kappa, T.ohi, T.olo);
+    DFDM_LAUNCH_CHECK();
+    DFDM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(d_level);
+    cudaFree(d_dir);
+    cudaFree(d_w);
+    cudaFree(d_sc);
+    for (auto &L : plan.levels) {
+      if (L.off.empty()) continue;
+      const int no = (int)L.off.size() / 3;
+      const cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)KP, (cuuint64_t)no};
+      const cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)KP * KP * 2};
+      const cuuint32_t box[3] = {(cuuint32_t)kK, (cuuint32_t)(KP / 2), 1};
+      const cuuint32_t es[3] = {1, 1, 1};
+      __half *bh = T.ohi + (size_t)L.op_base * KP * KP;
+      __half *bl = T.olo + (size_t)L.op_base * KP * KP;
+      encode(&T.map_ohi[L.level], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bh, dims, strides, box, es,
+             CU_TENSOR_MAP_SWIZZLE_32B);
+      encode(&T.map_olo[L.level], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bl, dims, strides, box, es,
+             CU_TENSOR_MAP_SWIZZLE_32B);
+    }
+  }
+  DFDM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+template <int O, int NP>
+static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) {
+  constexpr int N = O * O * O;
+  TcState &T = *plan.tc;
+  Timing &tm = plan.timing;
+  const int p = plan.depth, KP = T.KP;
+  const Tree &tt = plan.tt, &ts = plan.ts;
+  const bool far = plan.min_level <= p;
+  if (far) {
+    const LevelPlan &P = plan.levels[p];
+    const int nsl = (int)P.slot_dir.size();
+    {
+      PhaseScope sc(tm, kPhS2M, st);
+      DFDM_CUDA_TRY(cudaMemsetAsync(T.maxabs, 0, (p + 1) * sizeof(float), st));
+      for (int l = plan.min_level; l <= p; ++l) {
+        const size_t bytes = plan.levels[l].slot_dir.size() * ((size_t)1 << (3 * l)) * KP * sizeof(float);
+        DFDM_CUDA_TRY(cudaMemsetAsync(T.loc32[l], 0, bytes, st));
+      }
+      const size_t bytes = P.slot_dir.size() * ((size_t)1 << (3 * p)) * KP * sizeof(float);
+      DFDM_CUDA_TRY(cudaMemsetAsync(T.mom32[p], 0, bytes, st));
+      if (nsl > 0 && ts.nleaves > 0) {
+        k_s2m_f32<O><<<dim3((unsigned)ts.nleaves, nsl), 128, 0, st>>>(
+            T.sl, ts.n, ts.perm, x, ts.leaf_cell, ts.leaf_begin, ts.leaf_end, P.w,
+            plan.dir_vec_dev + plan.dir_vec_off[p], plan.kappa, T.mom32[p], 1ll << (3 * p), KP, T.maxabs + p);
+        DFDM_COUNT_LAUNCH(plan);
+      }
+    }
+    {
+      PhaseScope sc(tm, kPhM2M, st);
+      for (int l = p - 1; l >= plan.min_level; --l) {
+        const LevelPlan &L = plan.levels[l];
+        const int ns = (int)L.slot_dir.size();
+        if (ns == 0) continue;
+        const float2 *ph = plan.m2m_phase_off[l] >= 0 ? T.phase + plan.m2m_phase_off[l] : nullptr;
+        k_m2m_f32<O><<<dim3((unsigned)(1ll << (3 * l)), ns), 128, 0, st>>>(
+            T.mom32[l + 1], T.mom32[l], L.grid, plan.child_slot_dev + plan.child_slot_off[l], ph, ns, T.e1, KP,
+            T.maxabs + l);
+        DFDM_COUNT_LAUNCH(plan);
+      }
+    }
+    // split + M2L
+    for (int l = std::max(1, plan.min_level); l <= p; ++l) {
+      const LevelPlan &L = plan.levels[l];
+      if (L.off.empty()) continue;
+      {
+        PhaseScope sc(tm, kPhSplit, st);
+        const int64_t cnt = (int64_t)L.slot_dir.size() * (1ll << (3 * l)) * KP;
+        k_split<<<1184, 256, 0, st>>>(T.mom32[l], cnt, T.maxabs + l, T.mom_exp + l, T.mhi[l], T.mlo[l]);
+        DFDM_COUNT_LAUNCH(plan);
+      }
+      M2lArgs a;
+      a.alpha_ops = plan.m2l_ops + plan.m2l_ops_off[l * 9];
+      a.alpha_off = plan.m2l_aoff_dev + 9 * l;
+      a.op_off = plan.op_off_dev;
+      a.op_slot = plan.op_slot_dev;
+      a.op_base = L.op_base;
+      a.loc = T.loc32[l];
+      a.g = L.grid;
+      a.n = N;
+      a.KP = KP;
+      a.mom_exp = T.mom_exp + l;
+      a.op_exp = T.op_exp[l];
+      a.err = plan.err_flag;
+      const int gp = L.grid / 2;
+      const int tiles = ((gp + kTX - 1) / kTX) * ((gp + kTY - 1) / kTY) * ((gp + kTZ - 1) / kTZ);
+      const int smem = M2lSmem<NP>::kTotal;
+      DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      PhaseScope sc(tm, kPhM2L0 + l, st);
+      k_m2l_tc<NP><<<dim3(tiles, 8), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], T.map_ohi[l],
+                                                              T.map_olo[l], a);
+      DFDM_COUNT_LAUNCH(plan);
+    }
+    {
+      PhaseScope sc(tm, kPhL2L, st);
+      for (int l = plan.min_level; l < p; ++l) {
+        const LevelPlan &L = plan.levels[l];
+        const LevelPlan &C = plan.levels[l + 1];
+        const int nsp = (int)L.slot_dir.size(), nsc = (int)C.slot_dir.size();
+        if (nsp == 0 || nsc == 0) continue;
+        const float2 *ph = plan.m2m_phase_off[l] >= 0 ? T.phase + plan.m2m_phase_off[l] : nullptr;
+        k_l2l_f32<O><<<dim3((unsigned)(1ll << (3 * (l + 1))), nsc), 128, 0, st>>>(
+            T.loc32[l], T.loc32[l + 1], C.grid, plan.l2l_pslots_dev + plan.l2l_pslots_off[l],
+            plan.l2l_poff_dev + plan.l2l_poff_off[l], ph, nsp, T.e1, KP);
+        DFDM_COUNT_LAUNCH(plan);
+      }
+    }
+    PhaseScope sc(tm, kPhL2T, st);
+    if (nsl > 0 && tt.nleaves > 0) {
+      k_l2t_f32<O><<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, P.w,
+                                                         plan.dir_vec_dev + plan.dir_vec_off[p], nsl, plan.kappa,
+                                                         T.loc32[p], 1ll << (3 * p), KP, T.ysorted);
+      DFDM_COUNT_LAUNCH(plan);
+    } else {
+      DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));
+    }
+  } else {
+    DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));
+  }
+  PhaseScope sc(tm, kPhNear, st);
+  k_p2p_f32<<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
+                                                  T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end,
+                                                  1 << p, (float)plan.levels[p].w, plan.near_off_dev,
+                                                  (int)(plan.near_off.size() / 3), (float)plan.kappa, x, T.ysorted,
+                                                  y);
+  DFDM_COUNT_LAUNCH(plan);
+}
+
+void apply_tc(Plan &plan, const float2 *x, float2 *y, int nrhs, cudaStream_t st) {
+  for (int r = 0; r < nrhs; ++r) {
+    const float2 *xr = x + (int64_t)r * plan.ts.n;
+    float2 *yr = y + (int64_t)r * plan.tt.n;
+    switch (plan.order) {
+      case 2: apply_tc_o<2, 64>(plan, xr, yr, st); break;     // 2n = 16  -> KP 64
+      case 3: apply_tc_o<3, 64>(plan, xr, yr, st); break;     // 2n = 54  -> KP 64
+      case 4: apply_tc_o<4, 128>(plan, xr, yr, st); break;    // 2n = 128 -> KP 128
+      case 5: apply_tc_o<5, 256>(plan, xr, yr, st); break;    // 2n = 250 -> KP 256
+      case 6: apply_tc_o<6, 448>(plan, xr, yr, st); break;    // 2n = 432 -> KP 448
+      default: throw Error{DFDM_ERR_UNSUPPORTED, "tensor-core form supports orders 2..6"};
+    }
+  }
+}
+
+}  // namespace dfdm

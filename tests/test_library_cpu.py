@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI library (no GPU needed): it loads, exports every
+symbol include/dfdm.h declares, and its host-only calls behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2004_14229_gb300 as pkg
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dfdm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2004_14229_gb300._build import build_library
+    build_library()
+    return pkg.load_library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(dfdm_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 11
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(pkg.EXPORTED_SYMBOLS) == sorted(names)
+
+
+def test_params_default_and_version(lib):
+    p = pkg.Params()
+    assert lib.dfdm_params_default(ctypes.byref(p)) == 0
+    assert (p.order, p.max_depth, p.n_max, p.eta2, p.l_hf) == (5, 6, 0, 5.0, -2)
+    assert p.root_side == 1.0 and p.nrhs_max == 1
+    assert lib.dfdm_params_default(None) == 1
+    assert b"sm_103a" in lib.dfdm_version()
+    assert lib.dfdm_last_error()
+
+
+def test_invalid_arguments_return_status(lib):
+    import numpy as np
+    pts = np.random.default_rng(0).random((10, 3))
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(pts, pts, -1.0)
+    assert e.value.status == 1
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(pts, pts, 1.0, order=11)
+    assert e.value.status == 1
+    bad = pts.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(bad, pts, 1.0)
+    assert e.value.status == 1
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(pts + 2.0, pts, 1.0)          # outside the unit root cube
+    assert e.value.status == 1
+    assert lib.dfdm_plan_destroy(None) == 0
+    assert lib.dfdm_apply(None, None, None, 1, None) == 1
+
+
+def test_plan_without_gpu_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    pts = np.random.default_rng(0).random((10, 3))
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(pts, pts, 1.0, max_depth=2)
+    assert e.value.status in (2, 3)

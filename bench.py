@@ -1,0 +1,291 @@
+"""Benchmark: fast directional matrix-vector products per second on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision tc|fp64]
+
+A step is one full product y = A x (S2M, M2M, M2L, L2L, L2T, nearfield) of
+the named workload (default: 2^22 uniform targets and sources in [0, 1]^3,
+kappa = 128, tree depth 7, Chebyshev order 6) with 1 right-hand side, on
+inputs already resident in HBM.  The plan (trees, partition, operators) is
+built once before the timed region.  Prints one JSON line.
+
+--impl reference times the CPU oracle instead: the exact FP64 direct sum of
+Eq. (1) (plain C, OpenMP over the host cores) on a bounded sample of target
+rows per step, scaled to the whole product.
+
+With torchrun (N > 1) every rank runs an independent replica of the workload
+(the product is not sharded); the value is the total over all ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_14229_gb300.workloads import (SEED_X, WORKLOADS, complex_normal,  # noqa: E402
+                                              sample_rows, uniform_points)
+
+METRIC = "matvecs/s at N=4M, kappa=128, rel.err<=1e-6: tensor-core form vs plain FP64"
+UNIT = "matvecs/s"
+DEFAULT_WORKLOAD = "uniform-4M-k128-d7-o6"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_rows_per_sec(targets, sources, kappa, x, nrows):
+    from oracle.direct import direct_rows, direct_threads
+    rows = sample_rows(targets.shape[0], nrows, seed=5)
+    t0 = time.perf_counter()
+    direct_rows(targets, sources, kappa, x, rows)
+    dt = time.perf_counter() - t0
+    return nrows / dt, dt, direct_threads()
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    t = uniform_points(w["n"], 1)
+    s = uniform_points(w["n"], 2)
+    x = complex_normal(w["n"], SEED_X)
+    nrows = args.ref_rows
+    for _ in range(args.warmup):
+        _oracle_rows_per_sec(t, s, w["kappa"], x, max(8, nrows // 8))
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        _, dt, cores = _oracle_rows_per_sec(t, s, w["kappa"], x, nrows)
+        times.append(dt)
+    per_step = sum(times) / len(times)
+    value = (nrows / w["n"]) / per_step
+    sample = ("O_direct (FP64 C double loop, OpenMP) on %d of %d target rows x all %d sources per step, "
+              "scaled to the full product" % (nrows, w["n"], w["n"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **w},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2004_14229_gb300 as pkg
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = WORKLOADS[args.workload]
+    prec = pkg.TC_FP16X3 if args.precision == "tc" else pkg.FP64
+    cdt = np.complex64 if prec == pkg.TC_FP16X3 else np.complex128
+    tdt = torch.complex64 if prec == pkg.TC_FP16X3 else torch.complex128
+    t = uniform_points(w["n"], 1)
+    s = uniform_points(w["n"], 2)
+    x = complex_normal(w["n"], SEED_X)
+    t_setup = time.perf_counter()
+    plan = pkg.Plan(t, s, w["kappa"], order=w["order"], max_depth=w["depth"], precision=prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    st = plan.stats()
+    xd = torch.from_numpy(x.astype(cdt)).cuda()
+    yd = torch.empty(w["n"], dtype=tdt, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.apply(xd, yd)
+    torch.cuda.synchronize()
+    plan.check()
+
+    # ---------------------------------------------------------- timed region
+    plan.set_timing(True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    m2l_ms = [0.0] * 16
+    phases = {k: 0.0 for k in ("s2m_ms", "m2m_ms", "split_ms", "l2l_ms", "l2t_ms", "near_ms", "total_ms")}
+    launches = 0
+    for _ in range(args.steps):
+        plan.apply(xd, yd)
+        tm = plan.timing()       # waits for this step's phase events
+        for i in range(16):
+            m2l_ms[i] += tm["m2l_ms"][i]
+        for k in phases:
+            phases[k] += tm[k]
+        launches += tm["launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    plan.set_timing(False)
+    plan.check()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = world * args.steps / elapsed
+
+    # accuracy against the FP64 oracle on stored rows (written by the oracle)
+    err = None
+    gold = os.path.join(ROOT, "tests", "golden", "%s_rows.npz" % args.workload)
+    if os.path.exists(gold):
+        g = np.load(gold)
+        yv = yd.cpu().numpy()[g["rows"]]
+        err = float(np.linalg.norm(yv - g["y_fdm"]) / np.linalg.norm(g["y_fdm"]))
+
+    # ------------------------------------------------------------ end to end
+    xh = torch.from_numpy(x.astype(cdt)).pin_memory()
+    yh = torch.empty(w["n"], dtype=tdt).pin_memory()
+    plan.apply_host(xh.numpy(), yh.numpy())
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.apply_host(xh.numpy(), yh.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = world / e2e_s
+
+    # -------------------------------------------------------------- roofline
+    n = w["order"] ** 3
+    flops_step = 8.0 * n * n * st["n_coupling"]          # complex n x n MAC = 8 real flops
+    m2l_s = sum(m2l_ms) / 1e3 / args.steps
+    peaks, src = _peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0) if prec == pkg.TC_FP16X3 else 1.25
+    achieved = flops_step / m2l_s / 1e12
+    roofline = {"bound": "tensor" if prec == pkg.TC_FP16X3 else "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "k_m2l_tc" if prec == pkg.TC_FP16X3 else "k_m2l_fp64",
+                "peak_source": ("%s sustained bf16 (fp16 has the same nominal rate)" % src)
+                if prec == pkg.TC_FP16X3 else "nominal GB300 FP64",
+                "algorithmic_flops_per_step": flops_step, "m2l_ms_per_step": m2l_s * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x3+f32" if prec == pkg.TC_FP16X3 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_targets": w["n"], "n_sources": w["n"],
+                       "kappa": w["kappa"], "depth": w["depth"], "order": w["order"],
+                       "precision": args.precision, "nrhs": 1, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2": "inputs larger than L2 (coupling operators streamed every step)"},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+                    "d2h_bytes_per_step": yh.numel() * yh.element_size()},
+            "gpu_launches": launches,
+            "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+            "m2l_ms_per_level": [v / args.steps for v in m2l_ms[:w["depth"] + 1]],
+            "setup_s": setup_s, "n_coupling": st["n_coupling"], "n_stored_coupling": st["n_stored_coupling"],
+            "rel_err_vs_oracle_rows": err, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rps, dt, cores = _oracle_rows_per_sec(t, s, w["kappa"], x, args.ref_rows)
+        line["cpu_baseline"] = {"value": rps / w["n"], "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "O_direct (FP64 C double loop, OpenMP) on %d target rows x all %d "
+                                          "sources (%.1f s), scaled to the full product"
+                                          % (args.ref_rows, w["n"], dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="tc", choices=["tc", "fp64"])
+    ap.add_argument("--ref-rows", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -392,17 +392,20 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
 
 // ------------------------------------------------------------- M2L (TC)
 // One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
-// grid), all NP stacked outputs, one level.  Per K step of 16:
-//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi
-//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo
-// so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 hold the cross
-// terms X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one smem
-// buffer [Z | M_hi | M_lo]).  The tensor core truncates its FP32
-// accumulator towards zero after every instruction, so H is drained into an
-// FP32 shared-memory sum R (round to nearest) after every operator: no H
-// chain is longer than KP / 16 instructions.  X is 2^-11 of H and is drained
-// into R every kFlushOps operators; R goes to the FP32 local grid at the
-// same points and when the direction slot changes.
+// grid), all NP stacked outputs, one level.  The outputs form two halves of
+// NH = NP / 2 columns (two TMEM regions).  Per K step of 16 and half h:
+//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[h]
+//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[h]
+// so TMEM lanes 0..63 of region h hold H = M_hi O_hi and lanes 64..127 the
+// cross terms X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one
+// smem buffer [Z | M_hi | M_lo]).  The tensor core truncates its FP32
+// accumulator towards zero after every instruction, so H never accumulates
+// more than KSTEPS / kKsplit instructions: the MMAs of one operator run as
+// work units (K part, half), and after each unit four epilogue warps add
+// that region's H to an FP32 shared-memory sum R (round to nearest) and
+// clear it, while the MMAs already fill the other region.  X is 2^-11 of H;
+// it is added to R every kFlushOps operators and when the direction slot
+// changes, and R then goes to the FP32 local grid.
 struct M2lArgs {
   const int32_t *alpha_ops;   // level's op list (global op indices), per alpha
   const int32_t *alpha_off;   // 9 offsets into alpha_ops
@@ -421,29 +424,39 @@ struct M2lArgs {
 constexpr int kTM = 64;                   // targets per CTA
 constexpr int kTX = 4, kTY = 4, kTZ = 4;  // parent-grid block of a CTA
 constexpr int kK = 16;                    // K per stage (32-byte rows)
-constexpr int kSt = 3;                    // pipeline stages
-constexpr int kM2lWarps = 18;             // 0 TMA, 1 MMA, 2-3 X drain, 4.. H drain
+constexpr int kSt = 5;                    // pipeline stages
+constexpr int kKsplit = 2;                // K parts per operator (units per half)
+constexpr int kM2lWarps = 18;             // 0 TMA, 1 MMA, 2-3 X drain, 8 H warps
 constexpr int kM2lThreads = kM2lWarps * 32;
-constexpr int kEpiThreads = 10 * 32;      // warps 2, 3 and the eight H warps
+constexpr int kEpiWarps = 10;
+constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kFlushOps = 32;
 
 template <int NP>
 struct M2lSmem {
+  static constexpr int NH = NP / 2;
   static constexpr int kRowB = kK * 2;                 // bytes per operand row
   static constexpr int kZ = kTM * kRowB;               // zero rows
   static constexpr int kM = kTM * kRowB;               // 64 moment rows
-  static constexpr int kO = NP * kRowB;                // operator rows
+  static constexpr int kO = NH * kRowB;                // one half of the operator rows
   static constexpr int kOffMhi = kZ, kOffMlo = kZ + kM, kOffOhi = kZ + 2 * kM, kOffOlo = kZ + 2 * kM + kO;
   static constexpr int kStage = kZ + 2 * kM + 2 * kO;
+  static constexpr int kTx = 2 * kM + 2 * kO;          // bytes TMA brings per stage
   static constexpr int kR = kTM * NP * 4;              // FP32 running sums R[col][row]
   static constexpr int kTotal = kSt * kStage + kR + 1024;
   static_assert(kStage % 1024 == 0, "stage alignment");
 };
 
-// Epilogue warp roles: H warps are quarters 0 / 1 (lanes 0..63), four column
-// groups each; X warps 2 and 3 are quarters 2 / 3 (lanes 64..127).
-__device__ __forceinline__ int h_group(int warp) { return (warp >= 4 && warp < 20 && (warp & 3) < 2) ? (warp - 4) / 4 : -1; }
+// H warps: 4, 5, 8, 9 (region 0) and 12, 13, 16, 17 (region 1); lane
+// quarter q = warp & 3 in {0, 1}, column group g in {0, 1} of the region.
+__device__ __forceinline__ int h_index(int warp) {
+  switch (warp) {
+    case 4: return 0; case 5: return 1; case 8: return 2; case 9: return 3;
+    case 12: return 4; case 13: return 5; case 16: return 6; case 17: return 7;
+    default: return -1;
+  }
+}
 
 template <int NP>
 __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant__ CUtensorMap map_mhi,
@@ -452,16 +465,18 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
                                                           const __grid_constant__ CUtensorMap map_olo,
                                                           const M2lArgs args) {
   using S = M2lSmem<NP>;
-  constexpr int NH = NP / 2;          // N of one MMA (<= 256)
-  constexpr int KSTEPS = NP / kK;     // stages per operator (KP == NP)
-  constexpr int GCOLS = NP / 4;       // columns per H warp
+  constexpr int NH = NP / 2;               // N of one MMA (<= 256)
+  constexpr int KSTEPS = NP / kK;          // K steps per operator (KP == NP)
+  constexpr int USTEPS = KSTEPS / kKsplit; // K steps per unit
+  constexpr int GCOLS = NH / 2;            // columns per H warp
   constexpr uint32_t kTmemCols = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
   static_assert(NH % 16 == 0 && NH <= 256, "N half must be a multiple of 16, <= 256");
   static_assert(GCOLS % 16 == 0, "H warp column group must be a multiple of 16");
+  static_assert(KSTEPS % kKsplit == 0, "K steps must split evenly");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NP][kTM]
-  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full, acc_empty;
+  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full[2], acc_empty[2], grp_done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
@@ -487,8 +502,11 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       ptx::mbar_init(&full_bar[s], 1);
       ptx::mbar_init(&empty_bar[s], 1);
     }
-    ptx::mbar_init(&acc_full, 1);
-    ptx::mbar_init(&acc_empty, kEpiThreads / 32);
+    for (int h = 0; h < 2; ++h) {
+      ptx::mbar_init(&acc_full[h], 1);
+      ptx::mbar_init(&acc_empty[h], 4);
+    }
+    ptx::mbar_init(&grp_done, kEpiWarps);
     s_abort = 0;
     ptx::fence_mbar_init();
   }
@@ -517,18 +535,20 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
         const int y0 = 2 * Y0 + ay - args.op_off[3 * op + 1];
         const int z0 = 2 * Z0 + az - args.op_off[3 * op + 2];
         const int opl = op - args.op_base;
-        for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
-          const int st = it % kSt;
-          const uint32_t ph = (it / kSt) & 1;
-          if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
-          uint8_t *base = smem + st * S::kStage;
-          ptx::mbar_expect_tx(&full_bar[st], 2 * S::kM + 2 * S::kO);
-          ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
-          ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
-          ptx::tma_load_3d(base + S::kOffOhi, &map_ohi, &full_bar[st], kc * kK, 0, opl);
-          ptx::tma_load_3d(base + S::kOffOhi + S::kO / 2, &map_ohi, &full_bar[st], kc * kK, NH, opl);
-          ptx::tma_load_3d(base + S::kOffOlo, &map_olo, &full_bar[st], kc * kK, 0, opl);
-          ptx::tma_load_3d(base + S::kOffOlo + S::kO / 2, &map_olo, &full_bar[st], kc * kK, NH, opl);
+        for (int u = 0; u < 2 * kKsplit && ok; ++u) {
+          const int kh = u >> 1, h = u & 1;
+          for (int ks = 0; ks < USTEPS; ++ks, ++it) {
+            const int kc = kh * USTEPS + ks;
+            const int st = it % kSt;
+            const uint32_t ph = (it / kSt) & 1;
+            if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
+            uint8_t *base = smem + st * S::kStage;
+            ptx::mbar_expect_tx(&full_bar[st], S::kTx);
+            ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
+            ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
+            ptx::tma_load_3d(base + S::kOffOhi, &map_ohi, &full_bar[st], kc * kK, h * NH, opl);
+            ptx::tma_load_3d(base + S::kOffOlo, &map_olo, &full_bar[st], kc * kK, h * NH, opl);
+          }
         }
       }
       if (!ok) {
@@ -540,31 +560,46 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
       constexpr uint32_t idesc = ptx::idesc_f16_f32(128, NH);
-      uint32_t it = 0;
-      bool first = true, ok = true;
-      int j = 0;
-      for (int ii = i0; ii < i1 && ok; ++ii, ++j) {
-        for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
-          const int st = it % kSt;
-          const uint32_t ph = (it / kSt) & 1;
-          if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
-          ptx::tc_fence_after();
-          const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
-          const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
-          const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t d = tmem + h * NH;
-            ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi + h * (S::kO / 2)), idesc, first ? 0u : 1u);
-            ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo + h * (S::kO / 2)), idesc, 1u);
+      uint32_t it = 0, groups = 0;
+      uint32_t units[2] = {0, 0};   // units issued per region
+      bool ok = true;
+      int run = 0;
+      for (int ii = i0; ii < i1 && ok; ++ii) {
+        const int slot = args.op_slot[args.alpha_ops[ii]];
+        const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
+        for (int u = 0; u < 2 * kKsplit && ok; ++u) {
+          const int h = u & 1;
+          if (units[h] > 0) {   // region drained by the epilogue?
+            if (!ptx::mbar_wait(&acc_empty[h], (units[h] - 1) & 1, kWaitLimit)) { ok = false; break; }
+            ptx::tc_fence_after();
           }
-          first = false;
-          ptx::mma_commit(&empty_bar[st]);
+          const uint32_t d = tmem + h * NH;
+          for (int ks = 0; ks < USTEPS; ++ks, ++it) {
+            const int st = it % kSt;
+            const uint32_t ph = (it / kSt) & 1;
+            if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
+            const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
+            const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
+            const uint32_t init = (units[h] == 0 && ks == 0) ? 0u : 1u;
+            ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi), idesc, init);
+            ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo), idesc, 1u);
+            ptx::mma_commit(&empty_bar[st]);
+          }
+          if (!ok) break;
+          ptx::mma_commit(&acc_full[h]);
+          ++units[h];
         }
         if (!ok) break;
-        ptx::mma_commit(&acc_full);
-        if (!ptx::mbar_wait(&acc_empty, j & 1, kWaitLimit)) { ok = false; break; }
-        ptx::tc_fence_after();
+        ++run;
+        if (next_slot != slot || run >= kFlushOps) {
+          // X and R are drained after this operator: wait for the epilogue
+          if (!ptx::mbar_wait(&grp_done, groups & 1, kWaitLimit)) { ok = false; break; }
+          ptx::tc_fence_after();
+          ++groups;
+          run = 0;
+        }
       }
       if (!ok) {
         atomicExch(args.err, 1);
@@ -573,9 +608,9 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
     }
   } else {
     // ------------------------------------------------ epilogue
-    const int hg = h_group(warp);
+    const int hi = h_index(warp);
     const bool xw = (warp == 2 || warp == 3);
-    if (hg >= 0 || xw) {
+    if (hi >= 0 || xw) {
       const int q = warp & 3;                        // TMEM lane quarter
       const int r = (q & 1) * 32 + lane;             // target row 0..63
       const int ix = r % kTX, iy = (r / kTX) % kTY, iz = r / (kTX * kTY);
@@ -586,48 +621,54 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
       const int n = args.n;
       const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+      const int region = (hi >= 0) ? hi / 4 : -1;
+      const int c0 = (hi >= 0) ? region * NH + ((hi >> 1) & 1) * GCOLS : 0;   // first column of this H warp
+      const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      uint32_t drains = 0;   // units of this warp's region drained so far
       int run = 0;
-      int j = 0;
-      for (int ii = i0; ii < i1; ++ii, ++j) {
+      bool stop = false;
+      for (int ii = i0; ii < i1 && !stop; ++ii) {
         const int slot = args.op_slot[args.alpha_ops[ii]];
         const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
         ++run;
         const bool group_end = (next_slot != slot) || run >= kFlushOps;
-        // wait for the operator's MMAs; every epilogue warp then meets at a
-        // named barrier, so a give-up is seen by all of them at the same op
-        bool got = false;
-        {
-          const uint64_t t0 = ptx::global_ns();
-          for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
-            got = ptx::mbar_try_wait(&acc_full, j & 1);
-            if (!got && (t & 255) == 255 &&
-                (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
-              break;
-          }
-        }
-        if (!got) atomicExch(args.err, 1);
-        const bool stop = !got || *(volatile int *)&s_abort;
-        if (ptx::named_bar_or(2, kEpiThreads, stop)) break;   // same decision in every epilogue warp
-        ptx::tc_fence_after();
-        if (hg >= 0) {
-          // H -> R (round to nearest), then clear H
-          const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool bad = false;
+        if (hi >= 0) {
+          for (int u = 0; u < kKsplit && !bad; ++u, ++drains) {
+            bool got = false;
+            const uint64_t t0 = ptx::global_ns();
+            for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
+              got = ptx::mbar_try_wait(&acc_full[region], drains & 1);
+              if (!got && (t & 255) == 255 &&
+                  (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
+                break;
+            }
+            if (!got) { bad = true; break; }
+            ptx::tc_fence_after();
 #pragma unroll 1
-          for (int c = hg * GCOLS; c < (hg + 1) * GCOLS; c += 16) {
-            float v[16];
-            ptx::tmem_ld16(tmem + lane_addr + c, v);
-            ptx::tmem_ld_wait();
+            for (int c = c0; c < c0 + GCOLS; c += 16) {
+              float v[16];
+              ptx::tmem_ld16(tmem + lane_addr + c, v);
+              ptx::tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
-            ptx::tmem_st16(tmem + lane_addr + c, zero);
+              for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
+              ptx::tmem_st16(tmem + lane_addr + c, zero);
+            }
+            ptx::tmem_st_wait();
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acc_empty[region]);
           }
-          ptx::tmem_st_wait();
         }
+        if (bad) atomicExch(args.err, 1);
+        // one decision for all epilogue warps
+        stop = ptx::named_bar_or(2, kEpiThreads, bad || *(volatile int *)&s_abort);
+        if (stop) break;
         if (group_end) {
-          ptx::named_bar(1, kEpiThreads);
           if (xw) {
-            // X -> R, then clear X
-            const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            // X -> R for both regions, then clear X (every unit of this
+            // operator has completed: the H warps consumed all acc_full)
+            ptx::tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < NP; c += 16) {
               float v[16];
@@ -640,22 +681,23 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
             ptx::tmem_st_wait();
           }
           ptx::named_bar(1, kEpiThreads);
-          if (hg >= 0) {
-            // R -> local grid (scaled), then clear R
+          if (hi >= 0) {
+            // R -> local grid (scaled), then clear R; this warp owns rows of
+            // quarter q and columns [c0, c0 + GCOLS) of region `region`
             float *dst = args.loc + ((int64_t)slot * ncell + cell) * args.KP;
 #pragma unroll 1
-            for (int c = hg * GCOLS; c < (hg + 1) * GCOLS; ++c) {
+            for (int c = c0; c < c0 + GCOLS; ++c) {
               const int jj = (c < NH) ? c : c - NH;
               const float val = R[c * kTM + r];
               R[c * kTM + r] = 0.f;
               if (valid && jj < n) dst[(c < NH) ? jj : n + jj] += val * inv;
             }
           }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&grp_done);
           run = 0;
         }
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&acc_empty);
       }
     }
   }
@@ -670,8 +712,10 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
                                                  const int32_t *leaf_begin, const int32_t *leaf_end, double w,
                                                  const double *dir, int nslots, double kappa, const float *loc,
                                                  int64_t ncell, int KP, float2 *ysorted) {
+  // Products in FP32, the n-term sum in FP64 (its cancellation would cost
+  // ~sqrt(n) FP32 roundings relative to the result otherwise).
   constexpr int N = O * O * O;
-  __shared__ float2 red[4];
+  __shared__ double2 red[4];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const float inv_h = (float)(2.0 / w);
@@ -682,43 +726,48 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
     lagrange1f<O>(y0 * inv_h, lx);
     lagrange1f<O>(y1 * inv_h, ly);
     lagrange1f<O>(y2 * inv_h, lz);
-    float2 tot = make_float2(0.f, 0.f);
+    double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
       const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
-      float sr = 0.f, si = 0.f;
+      double sr = 0.0, si = 0.0;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const int kx = k % O, ky = (k / O) % O, kz = k / (O * O);
         const float l = lx[kx] * ly[ky] * lz[kz];
-        sr = fmaf(l, src[k], sr);
-        si = fmaf(l, src[N + k], si);
+        sr += (double)(l * src[k]);
+        si += (double)(l * src[N + k]);
       }
       const float2 ph = cexpi_reduced(kappa * ((double)y0 * dir[3 * slot] + (double)y1 * dir[3 * slot + 1] +
                                                (double)y2 * dir[3 * slot + 2]));
-      tot.x += sr * ph.x - si * ph.y;
-      tot.y += sr * ph.y + si * ph.x;
+      tx += sr * ph.x - si * ph.y;
+      ty += sr * ph.y + si * ph.x;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      tot.x += __shfl_down_sync(0xffffffffu, tot.x, o);
-      tot.y += __shfl_down_sync(0xffffffffu, tot.y, o);
+      tx += __shfl_down_sync(0xffffffffu, tx, o);
+      ty += __shfl_down_sync(0xffffffffu, ty, o);
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(tx, ty);
     __syncthreads();
     if (threadIdx.x == 0) {
-      float2 r = red[0];
+      double2 r = red[0];
       for (int i = 1; i < 4; ++i) {
         r.x += red[i].x;
         r.y += red[i].y;
       }
-      ysorted[p] = r;
+      ysorted[p] = make_float2((float)r.x, (float)r.y);
     }
     __syncthreads();
   }
 }
 
 // ----------------------------------------------------- nearfield (FP32)
-// One block per target leaf; source points of each nearfield leaf staged in
-// shared memory; leaf-local coordinates keep |x - y| accurate in FP32
-// (m_t - m_s = w d is exact).
+// One block per target leaf.  Each thread owns up to kP2pT targets of the
+// leaf (strided by the block size); the source points of every nearfield
+// leaf are staged through shared memory in chunks of 128.  Positions are
+// leaf-local FP32 (m_t - m_s = w d is exact), so |x - y| keeps FP32 relative
+// accuracy.  Each chunk's sum is formed in FP32 and added to an FP64 total,
+// so long source lists (512-point leaves) do not accumulate FP32 rounding.
+constexpr int kP2pT = 4;
+
 __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
                                                  const int32_t *leaf_cell, const int32_t *leaf_begin,
                                                  const int32_t *leaf_end, const float *sl, int64_t ns,
@@ -726,23 +775,26 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
                                                  const int32_t *sb, const int32_t *se, int g, float w,
                                                  const int32_t *near_off, int nnear, float kappa,
                                                  const float2 *x, const float2 *ysorted, float2 *y) {
-  __shared__ float4 sp[128];   // x, y, z (local, shifted), unused
+  __shared__ float4 sp[128];
   __shared__ float2 sv[128];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
-  for (int p0 = b; p0 < e; p0 += blockDim.x) {
-    const int p = p0 + threadIdx.x;
-    const bool act = p < e;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-    float2 acc = make_float2(0.f, 0.f);
-    if (act) {
-      x0 = tl[p];
-      x1 = tl[nt + p];
-      x2 = tl[2 * nt + p];
-      acc = ysorted[p];
+  for (int p0 = b; p0 < e; p0 += kP2pT * blockDim.x) {
+    float px[kP2pT], py[kP2pT], pz[kP2pT];
+    double ar[kP2pT], ai[kP2pT];
+    bool act[kP2pT];
+#pragma unroll
+    for (int u = 0; u < kP2pT; ++u) {
+      const int p = p0 + u * blockDim.x + threadIdx.x;
+      act[u] = p < e;
+      px[u] = act[u] ? tl[p] : 0.f;
+      py[u] = act[u] ? tl[nt + p] : 0.f;
+      pz[u] = act[u] ? tl[2 * nt + p] : 0.f;
+      ar[u] = 0.0;
+      ai[u] = 0.0;
     }
     for (int i = 0; i < nnear; ++i) {
       const int dx = near_off[3 * i], dy = near_off[3 * i + 1], dz = near_off[3 * i + 2];
@@ -761,24 +813,36 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
           sv[threadIdx.x] = x[sperm[q]];
         }
         __syncthreads();
-        if (act) {
+#pragma unroll
+        for (int u = 0; u < kP2pT; ++u) {
+          if (!act[u]) continue;
+          float cr = 0.f, ci = 0.f;
           for (int k = 0; k < cnt; ++k) {
-            const float d0 = x0 - sp[k].x, d1 = x1 - sp[k].y, d2 = x2 - sp[k].z;
-            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const float4 q = sp[k];
+            const float d0 = px[u] - q.x, d1 = py[u] - q.y, d2 = pz[u] - q.z;
+            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
             if (r2 == 0.f) continue;   // coincident points (zero diagonal)
             const float ir = rsqrtf(r2);
-            const float r = r2 * ir;
-            float s, c;
-            sincosf(kappa * r, &s, &c);
+            float sn, cs;
+            sincosf(kappa * (r2 * ir), &sn, &cs);
             const float sc = inv4pi * ir;
             const float2 v = sv[k];
-            acc.x = fmaf(sc, c * v.x - s * v.y, acc.x);
-            acc.y = fmaf(sc, c * v.y + s * v.x, acc.y);
+            cr = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr);
+            ci = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci);
           }
+          ar[u] += (double)cr;
+          ai[u] += (double)ci;
         }
       }
     }
-    if (act) y[tperm[p]] = acc;
+#pragma unroll
+    for (int u = 0; u < kP2pT; ++u) {
+      const int p = p0 + u * blockDim.x + threadIdx.x;
+      if (act[u]) {
+        const float2 f = ysorted[p];
+        y[tperm[p]] = make_float2((float)(ar[u] + (double)f.x), (float)(ai[u] + (double)f.y));
+      }
+    }
   }
 }
 

@@ -179,6 +179,24 @@ dfdm_status dfdm_plan_export_offsets(dfdm_plan plan, int level,
                                      int alpha_index, int32_t *count,
                                      int32_t *offsets, int32_t *dirs);
 
+/* Rows of the exact product of Eq. (1) by direct summation in FP64 on the GPU
+ * (the direct computation Sect. 4 compares the method with):
+ *     y[r] = sum_k A[rows[r], k] x[k],  r = 0 .. nrows-1,
+ * a coincident target/source pair contributing 0.  No plan is needed.
+ * targets (n_t x 3), sources (n_s x 3): DEVICE doubles, row-major; x: DEVICE
+ * complex128, n_s entries; rows: DEVICE int64, nrows entries; y: DEVICE
+ * complex128, nrows entries, overwritten.  A row index outside [0, n_t)
+ * gives NaN in its y entry.  The sources are split into chunks summed by
+ * separate blocks; the partial sums go to a scratch array of at most
+ * 64 x nrows complex128 that this call allocates and frees in stream order
+ * (cudaMallocAsync / cudaFreeAsync on `stream`).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL pointer, n_t, n_s or nrows < 1, kappa not > 0),
+ * OOM, CUDA. */
+dfdm_status dfdm_direct_rows(const double *targets, int64_t n_t,
+                             const double *sources, int64_t n_s, double kappa,
+                             const void *x, const int64_t *rows, int64_t nrows,
+                             void *y, void *stream);
+
 /* Frees the plan and everything it owns; NULL is allowed. */
 dfdm_status dfdm_plan_destroy(dfdm_plan plan);
 

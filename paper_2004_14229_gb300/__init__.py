@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_params_default", "dfdm_plan_create", "dfdm_apply", "dfdm_apply_host",
     "dfdm_plan_check", "dfdm_plan_stats", "dfdm_plan_export_tree",
     "dfdm_plan_export_offsets", "dfdm_plan_destroy", "dfdm_last_error", "dfdm_version",
-    "dfdm_plan_set_timing", "dfdm_plan_timing",
+    "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows",
 ]
 
 
@@ -83,6 +83,7 @@ def load_library():
         "dfdm_plan_export_offsets": [vp, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, vp],
         "dfdm_plan_destroy": [vp],
         "dfdm_plan_set_timing": [vp, i32],
+        "dfdm_direct_rows": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_plan_timing": [vp, ctypes.POINTER(Timing)],
         "dfdm_last_error": [],
         "dfdm_version": [],
@@ -112,6 +113,30 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def direct_rows(targets, sources, kappa, x, rows, stream=None):
+    """Rows of the exact product of Eq. (1), FP64 on the GPU (no plan).
+
+    targets, sources: CUDA float64 tensors (N, 3); x: CUDA complex128 (n_s,);
+    rows: CUDA int64 (nrows,).  Returns a CUDA complex128 tensor (nrows,).
+    """
+    import torch
+    t = targets.contiguous()
+    s = sources.contiguous()
+    xx = x.contiguous()
+    r = rows.contiguous()
+    for name, v, dt in (("targets", t, torch.float64), ("sources", s, torch.float64),
+                        ("x", xx, torch.complex128), ("rows", r, torch.int64)):
+        if not (v.is_cuda and v.dtype == dt):
+            raise TypeError("%s must be a CUDA tensor of dtype %s" % (name, dt))
+    y = torch.empty(r.shape[0], dtype=torch.complex128, device=xx.device)
+    lib = load_library()
+    _check(lib.dfdm_direct_rows(ctypes.c_void_p(t.data_ptr()), t.shape[0], ctypes.c_void_p(s.data_ptr()),
+                                s.shape[0], float(kappa), ctypes.c_void_p(xx.data_ptr()),
+                                ctypes.c_void_p(r.data_ptr()), r.shape[0], ctypes.c_void_p(y.data_ptr()),
+                                _stream_handle(stream)))
+    return y
 
 
 class Plan:

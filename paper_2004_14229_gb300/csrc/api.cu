@@ -368,6 +368,30 @@ dfdm_status dfdm_plan_export_offsets(dfdm_plan plan, int level, int alpha_index,
   return DFDM_OK;
 }
 
+dfdm_status dfdm_direct_rows(const double *targets, int64_t n_t, const double *sources, int64_t n_s,
+                             double kappa, const void *x, const int64_t *rows, int64_t nrows, void *y,
+                             void *stream) {
+  if (!targets || !sources || !x || !rows || !y) return fail(DFDM_ERR_INVALID_ARG, "NULL argument");
+  if (n_t < 1 || n_s < 1 || nrows < 1) return fail(DFDM_ERR_INVALID_ARG, "n_t, n_s and nrows must be >= 1");
+  if (!(kappa > 0) || !std::isfinite(kappa)) return fail(DFDM_ERR_INVALID_ARG, "kappa must be finite and > 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> dfdm_status {
+    const int nchunk = direct_chunks(nrows, n_s);
+    double2 *scratch = nullptr;
+    DFDM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&scratch),
+                                  (size_t)nchunk * nrows * sizeof(double2), st));
+    try {
+      direct_rows(targets, n_t, sources, n_s, kappa, static_cast<const double2 *>(x), rows, nrows,
+                  static_cast<double2 *>(y), scratch, nchunk, st);
+    } catch (...) {
+      cudaFreeAsync(scratch, st);
+      throw;
+    }
+    DFDM_CUDA_TRY(cudaFreeAsync(scratch, st));
+    return DFDM_OK;
+  });
+}
+
 dfdm_status dfdm_plan_destroy(dfdm_plan plan) {
   if (!plan) return DFDM_OK;
   plan->p.free_all();

@@ -223,6 +223,11 @@ int default_l_hf(double kappa, double root_side, int p);
 void build_levels(Plan &plan);
 int face_index(int l_hf, int level, const int d[3]);
 void direction_vector(int l_hf, int level, int j, double out[3]);
+// direct.cu
+int direct_chunks(int64_t nrows, int64_t ns);
+void direct_rows(const double *tgt, int64_t nt, const double *src, int64_t ns, double kappa, const double2 *x,
+                 const int64_t *rows, int64_t nrows, double2 *y, double2 *scratch, int nchunk,
+                 cudaStream_t st);
 // fp64.cu
 void build_operators_fp64(Plan &plan, cudaStream_t st);
 void count_pairs(Plan &plan, cudaStream_t st);

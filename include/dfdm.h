@@ -197,6 +197,35 @@ dfdm_status dfdm_direct_rows(const double *targets, int64_t n_t,
                              const void *x, const int64_t *rows, int64_t nrows,
                              void *y, void *stream);
 
+/* dfdm_direct_rows for callers that must not allocate device memory.
+ *
+ * The paper has no counterpart of this call; it exists for users of the
+ * library.  Some callers cannot allocate device memory at the moment they
+ * need these rows: a process whose device memory is reserved by another
+ * framework's caching allocator (a fresh allocation would fail or fragment
+ * that pool), or a latency-bound loop that must not let an allocation call
+ * synchronise or stall the device.  This variant computes exactly what
+ * dfdm_direct_rows computes, with the same arguments and the same kernel,
+ * and allocates nothing: its partial sums go to a fixed scratch array that
+ * the library places in device memory when it is loaded, 2^18 complex128
+ * entries (4 MiB) that every GPU using the library keeps until the process
+ * exits.  The caller still provides every input and output buffer.
+ *
+ * Limit: nrows <= 262144 (2^18); larger requests return DFDM_ERR_INVALID_ARG
+ * and touch nothing.  The first call on each device looks up the scratch
+ * array's device address (with that device current) and caches it; make that
+ * first call before any stream capture on the device.  All calls share the
+ * one array, which keeps the last call's partial sums (every entry a call
+ * reads it first writes, so nothing needs clearing): two calls whose work
+ * overlaps on a GPU (other streams, other threads) race on it and must be
+ * ordered by the caller.  Asynchronous on `stream`.  Errors as
+ * dfdm_direct_rows, plus CUDA if the address lookup fails. */
+dfdm_status dfdm_direct_rows_noalloc(const double *targets, int64_t n_t,
+                                     const double *sources, int64_t n_s,
+                                     double kappa, const void *x,
+                                     const int64_t *rows, int64_t nrows,
+                                     void *y, void *stream);
+
 /* Frees the plan and everything it owns; NULL is allowed. */
 dfdm_status dfdm_plan_destroy(dfdm_plan plan);
 

@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_params_default", "dfdm_plan_create", "dfdm_apply", "dfdm_apply_host",
     "dfdm_plan_check", "dfdm_plan_stats", "dfdm_plan_export_tree",
     "dfdm_plan_export_offsets", "dfdm_plan_destroy", "dfdm_last_error", "dfdm_version",
-    "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows",
+    "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows", "dfdm_direct_rows_noalloc",
 ]
 
 
@@ -84,6 +84,7 @@ def load_library():
         "dfdm_plan_destroy": [vp],
         "dfdm_plan_set_timing": [vp, i32],
         "dfdm_direct_rows": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
+        "dfdm_direct_rows_noalloc": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_plan_timing": [vp, ctypes.POINTER(Timing)],
         "dfdm_last_error": [],
         "dfdm_version": [],
@@ -115,11 +116,13 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def direct_rows(targets, sources, kappa, x, rows, stream=None):
+def direct_rows(targets, sources, kappa, x, rows, stream=None, y=None, noalloc=False):
     """Rows of the exact product of Eq. (1), FP64 on the GPU (no plan).
 
     targets, sources: CUDA float64 tensors (N, 3); x: CUDA complex128 (n_s,);
-    rows: CUDA int64 (nrows,).  Returns a CUDA complex128 tensor (nrows,).
+    rows: CUDA int64 (nrows,).  Returns a CUDA complex128 tensor (nrows,)
+    (`y` if given).  noalloc=True calls dfdm_direct_rows_noalloc, which uses
+    the library's fixed device scratch instead of allocating (nrows <= 2^18).
     """
     import torch
     t = targets.contiguous()
@@ -130,12 +133,14 @@ def direct_rows(targets, sources, kappa, x, rows, stream=None):
                         ("x", xx, torch.complex128), ("rows", r, torch.int64)):
         if not (v.is_cuda and v.dtype == dt):
             raise TypeError("%s must be a CUDA tensor of dtype %s" % (name, dt))
-    y = torch.empty(r.shape[0], dtype=torch.complex128, device=xx.device)
+    if y is None:
+        y = torch.empty(r.shape[0], dtype=torch.complex128, device=xx.device)
     lib = load_library()
-    _check(lib.dfdm_direct_rows(ctypes.c_void_p(t.data_ptr()), t.shape[0], ctypes.c_void_p(s.data_ptr()),
-                                s.shape[0], float(kappa), ctypes.c_void_p(xx.data_ptr()),
-                                ctypes.c_void_p(r.data_ptr()), r.shape[0], ctypes.c_void_p(y.data_ptr()),
-                                _stream_handle(stream)))
+    fn = lib.dfdm_direct_rows_noalloc if noalloc else lib.dfdm_direct_rows
+    _check(fn(ctypes.c_void_p(t.data_ptr()), t.shape[0], ctypes.c_void_p(s.data_ptr()),
+              s.shape[0], float(kappa), ctypes.c_void_p(xx.data_ptr()),
+              ctypes.c_void_p(r.data_ptr()), r.shape[0], ctypes.c_void_p(y.data_ptr()),
+              _stream_handle(stream)))
     return y
 
 

@@ -392,6 +392,26 @@ dfdm_status dfdm_direct_rows(const double *targets, int64_t n_t, const double *s
   });
 }
 
+dfdm_status dfdm_direct_rows_noalloc(const double *targets, int64_t n_t, const double *sources, int64_t n_s,
+                                     double kappa, const void *x, const int64_t *rows, int64_t nrows, void *y,
+                                     void *stream) {
+  if (!targets || !sources || !x || !rows || !y) return fail(DFDM_ERR_INVALID_ARG, "NULL argument");
+  if (n_t < 1 || n_s < 1 || nrows < 1) return fail(DFDM_ERR_INVALID_ARG, "n_t, n_s and nrows must be >= 1");
+  if (!(kappa > 0) || !std::isfinite(kappa)) return fail(DFDM_ERR_INVALID_ARG, "kappa must be finite and > 0");
+  if (nrows > kNoAllocScratchEntries)
+    return fail(DFDM_ERR_INVALID_ARG, "nrows exceeds the fixed scratch of dfdm_direct_rows_noalloc (262144 rows)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> dfdm_status {
+    // as many source chunks as dfdm_direct_rows uses, capped by the scratch size
+    const int nchunk =
+        (int)std::max<int64_t>(1, std::min<int64_t>(direct_chunks(nrows, n_s), kNoAllocScratchEntries / nrows));
+    double2 *scratch = noalloc_scratch();
+    direct_rows(targets, n_t, sources, n_s, kappa, static_cast<const double2 *>(x), rows, nrows,
+                static_cast<double2 *>(y), scratch, nchunk, st);
+    return DFDM_OK;
+  });
+}
+
 dfdm_status dfdm_plan_destroy(dfdm_plan plan) {
   if (!plan) return DFDM_OK;
   plan->p.free_all();

@@ -224,7 +224,12 @@ void build_levels(Plan &plan);
 int face_index(int l_hf, int level, const int d[3]);
 void direction_vector(int l_hf, int level, int j, double out[3]);
 // direct.cu
+// Fixed scratch of dfdm_direct_rows_noalloc: complex128 entries (4 MiB),
+// enough for nrows x chunks partial sums with nrows <= this count.
+constexpr int64_t kNoAllocScratchEntries = (int64_t)1 << 18;
+constexpr int kMaxDevicesNoAlloc = 64;
 int direct_chunks(int64_t nrows, int64_t ns);
+double2 *noalloc_scratch();
 void direct_rows(const double *tgt, int64_t nt, const double *src, int64_t ns, double kappa, const double2 *x,
                  const int64_t *rows, int64_t nrows, double2 *y, double2 *scratch, int nchunk,
                  cudaStream_t st);

@@ -5,6 +5,8 @@
 // block (row tile, chunk) forms the partial sums of its rows over its chunk
 // in a scratch array partial[chunk][row] (one write per entry, so the scratch
 // needs no clearing), and a second kernel adds the chunks in a fixed order.
+#include <mutex>
+
 #include "dfdm_internal.cuh"
 
 namespace dfdm {
@@ -86,6 +88,34 @@ int direct_chunks(int64_t nrows, int64_t ns) {
   c = std::max<int64_t>(1, std::min<int64_t>(c, 64));
   c = std::min<int64_t>(c, std::max<int64_t>(1, ns / kSrcTile));
   return (int)c;
+}
+
+// ------------------------------------------------ fixed scratch (no allocation)
+// Scratch of dfdm_direct_rows_noalloc: a file-scope device array that every
+// GPU loading the library holds until the process exits.  Host code only
+// sees a stand-in symbol for it; the device address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+namespace {
+__device__ __align__(256) static double2 g_direct_scratch[kNoAllocScratchEntries];
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevicesNoAlloc] = {};
+}  // namespace
+
+double2 *noalloc_scratch() {
+  int dev = 0;
+  DFDM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevicesNoAlloc)
+    throw Error{DFDM_ERR_UNSUPPORTED, "device ordinal beyond the no-alloc scratch table"};
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_direct_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      throw Error{DFDM_ERR_CUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") +
+                                     cudaGetErrorString(e)};
+    g_scratch_addr[dev] = p;
+  }
+  return static_cast<double2 *>(g_scratch_addr[dev]);
 }
 
 void direct_rows(const double *tgt, int64_t nt, const double *src, int64_t ns, double kappa, const double2 *x,

@@ -30,8 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2004_14229_gb300.workloads import (SEED_X, WORKLOADS, complex_normal,  # noqa: E402
-                                              sample_rows, uniform_points)
+from paper_2004_14229_gb300.workloads import WORKLOADS, sample_rows, workload  # noqa: E402
 
 METRIC = "matvecs/s at N=4M, kappa=128, rel.err<=1e-6: tensor-core form vs plain FP64"
 UNIT = "matvecs/s"
@@ -102,6 +101,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _config(args, w, world):
+    return {"workload": args.workload, "n_targets": w["n"], "n_sources": w["n"], "kappa": w["kappa"],
+            "max_depth": w["depth"], "n_max": w.get("n_max", 0), "order": w["order"],
+            "root_side": w["root"][1], "precision": args.precision, "nrhs": 1,
+            "parallelism": "replicas" if world > 1 else "1gpu",
+            "l2": "inputs larger than L2 (coupling operators streamed every step)"}
+
+
 def _oracle_rows_per_sec(targets, sources, kappa, x, nrows):
     from oracle.direct import direct_rows, direct_threads
     rows = sample_rows(targets.shape[0], nrows, seed=5)
@@ -115,10 +122,7 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    w = WORKLOADS[args.workload]
-    t = uniform_points(w["n"], 1)
-    s = uniform_points(w["n"], 2)
-    x = complex_normal(w["n"], SEED_X)
+    t, s, x, w = workload(args.workload)
     nrows = args.ref_rows
     for _ in range(args.warmup):
         _oracle_rows_per_sec(t, s, w["kappa"], x, max(8, nrows // 8))
@@ -134,7 +138,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, **w},
+            "data": "synthetic", "config": _config(args, w, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -151,15 +155,13 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = WORKLOADS[args.workload]
+    t, s, x, w = workload(args.workload)
     prec = pkg.TC_FP16X3 if args.precision == "tc" else pkg.FP64
     cdt = np.complex64 if prec == pkg.TC_FP16X3 else np.complex128
     tdt = torch.complex64 if prec == pkg.TC_FP16X3 else torch.complex128
-    t = uniform_points(w["n"], 1)
-    s = uniform_points(w["n"], 2)
-    x = complex_normal(w["n"], SEED_X)
     t_setup = time.perf_counter()
-    plan = pkg.Plan(t, s, w["kappa"], order=w["order"], max_depth=w["depth"], precision=prec)
+    plan = pkg.Plan(t, s, w["kappa"], order=w["order"], max_depth=w["depth"], n_max=w.get("n_max", 0),
+                    root=w["root"], precision=prec)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     st = plan.stats()
@@ -228,27 +230,40 @@ def run_ours(args):
     e2e_value = world / e2e_s
 
     # -------------------------------------------------------------- roofline
+    # dominant kernel: M2L (tensor cores) or, with large leaves, the nearfield
     n = w["order"] ** 3
-    flops_step = 8.0 * n * n * st["n_coupling"]          # complex n x n MAC = 8 real flops
-    m2l_s = sum(m2l_ms) / 1e3 / args.steps
     peaks, src = _peaks()
-    peak = peaks.get("bf16_tflops_sustained", 1700.0) if prec == pkg.TC_FP16X3 else 1.25
-    achieved = flops_step / m2l_s / 1e12
-    roofline = {"bound": "tensor" if prec == pkg.TC_FP16X3 else "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "kernel": "k_m2l_tc" if prec == pkg.TC_FP16X3 else "k_m2l_fp64",
-                "peak_source": ("%s sustained bf16 (fp16 has the same nominal rate)" % src)
-                if prec == pkg.TC_FP16X3 else "nominal GB300 FP64",
-                "algorithmic_flops_per_step": flops_step, "m2l_ms_per_step": m2l_s * 1e3}
+    m2l_s = sum(m2l_ms) / 1e3 / args.steps
+    near_s = phases["near_ms"] / 1e3 / args.steps
+    if m2l_s >= near_s:
+        flops_step = 8.0 * n * n * st["n_coupling"]          # complex n x n MAC = 8 real flops
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) if prec == pkg.TC_FP16X3 else 1.25
+        achieved = flops_step / m2l_s / 1e12
+        roofline = {"bound": "tensor" if prec == pkg.TC_FP16X3 else "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_m2l_tc" if prec == pkg.TC_FP16X3 else "k_m2l_fp64",
+                    "peak_source": ("%s sustained bf16 (fp16 has the same nominal rate)" % src)
+                    if prec == pkg.TC_FP16X3 else "nominal GB300 FP64",
+                    "algorithmic_flops_per_step": flops_step, "m2l_ms_per_step": m2l_s * 1e3}
+    else:
+        # 20 FP32 flops per pair (differences, |r|, kappa r, scale, complex
+        # multiply-add) + rsqrt, sin, cos; peak: 152 SMs x 128 FP32 lanes x 2
+        # flops at the sampled SM clock
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        pairs = float(st["nf_entries"])
+        achieved = 20.0 * pairs / near_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_p2p_f32" if prec == pkg.TC_FP16X3 else "k_p2p_fp64",
+                    "peak_source": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 flops x sampled SM clock",
+                    "pairs_per_step": pairs, "near_ms_per_step": near_s * 1e3}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f16x3+f32" if prec == pkg.TC_FP16X3 else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_targets": w["n"], "n_sources": w["n"],
-                       "kappa": w["kappa"], "depth": w["depth"], "order": w["order"],
-                       "precision": args.precision, "nrhs": 1, "parallelism": "replicas" if world > 1 else "1gpu",
-                       "l2": "inputs larger than L2 (coupling operators streamed every step)"},
+            "config": _config(args, w, world),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xh.numel() * xh.element_size(),
                     "d2h_bytes_per_step": yh.numel() * yh.element_size()},

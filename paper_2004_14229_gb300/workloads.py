@@ -21,10 +21,15 @@ SEED_ROWS = 4
 
 # Named workloads: point count, wave number, tree depth, Chebyshev order
 # (nodes per axis), root cube [0, 1]^3, eta2 = 5, l_hf by the default rule.
+# The "paper-grid" workloads are the setting of Sect. 4 / Table 1: the 8^k
+# tensor grid in [-1, 1]^3 as targets and sources (P_S = P_T), kappa =
+# 0.1 2^k, n_max = 512 (depth k - 3, 512 points per leaf), m = 4.
 WORKLOADS = {
     "uniform-8k-k16-d4-o4": dict(n=8192, kappa=16.0, depth=4, order=4),
     "uniform-1M-k64-d6-o5": dict(n=1 << 20, kappa=64.0, depth=6, order=5),
     "uniform-4M-k128-d7-o6": dict(n=1 << 22, kappa=128.0, depth=7, order=6),
+    "paper-grid-k6": dict(n=8 ** 6, kappa=6.4, depth=10, order=5, grid=6, n_max=512),
+    "paper-grid-k7": dict(n=8 ** 7, kappa=12.8, depth=10, order=5, grid=7, n_max=512),
 }
 
 
@@ -64,9 +69,17 @@ def tensor_grid(k):
 
 
 def workload(name):
-    """(targets, sources, x, params) of a named workload."""
-    w = WORKLOADS[name]
-    t = uniform_points(w["n"], SEED_TARGETS)
-    s = uniform_points(w["n"], SEED_SOURCES)
+    """(targets, sources, x, params) of a named workload; params also holds
+    the root cube ("root": (lo, side)) and n_max."""
+    w = dict(WORKLOADS[name])
+    if "grid" in w:
+        t = tensor_grid(w["grid"])
+        s = t
+        w["root"] = ((-1.0, -1.0, -1.0), 2.0)
+    else:
+        t = uniform_points(w["n"], SEED_TARGETS)
+        s = uniform_points(w["n"], SEED_SOURCES)
+        w["root"] = ((0.0, 0.0, 0.0), 1.0)
+        w.setdefault("n_max", 0)
     x = complex_normal(w["n"], SEED_X)
-    return t, s, x, dict(w)
+    return t, s, x, w

@@ -15,6 +15,12 @@ rows per step, scaled to the whole product.
 
 With torchrun (N > 1) every rank runs an independent replica of the workload
 (the product is not sharded); the value is the total over all ranks.
+
+--batch P times the batched form instead: P independent problems (N
+log-uniform in [1e4, 1e6], kappa log-uniform in [8, 256], uniform / Gaussian /
+shell points, Chebyshev order 5, tree depth ceil(log8(N / 64))), each with 16
+complex64 right-hand sides, applied together from one CUDA graph; the value is
+right-hand-side products per second.
 """
 import argparse
 import json
@@ -271,6 +277,7 @@ def run_ours(args):
             "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
             "m2l_ms_per_level": [v / args.steps for v in m2l_ms[:w["depth"] + 1]],
             "setup_s": setup_s, "n_coupling": st["n_coupling"], "n_stored_coupling": st["n_stored_coupling"],
+            "n_coupling_per_level": st["level_coupling"][:w["depth"] + 1],
             "rel_err_vs_oracle_rows": err, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rps, dt, cores = _oracle_rows_per_sec(t, s, w["kappa"], x, args.ref_rows)
@@ -286,6 +293,118 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    import torch
+
+    import paper_2004_14229_gb300 as pkg
+    from paper_2004_14229_gb300.workloads import batch_problems
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    nrhs, order = 16, 5
+    probs = batch_problems(args.batch, nrhs=nrhs)
+    t_setup = time.perf_counter()
+    batch = pkg.Batch(probs, order=order, root="bounding", precision=pkg.TC_FP16X3, nrhs_max=nrhs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    stats = [pl.stats() for pl in batch.plans]
+    xs = [torch.from_numpy(p["x"].astype(np.complex64)).cuda() for p in probs]
+    ys = [torch.empty((nrhs, p["targets"].shape[0]), dtype=torch.complex64, device="cuda") for p in probs]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.apply(xs, ys)
+    torch.cuda.synchronize()
+    batch.check()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.apply(xs, ys)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    batch.check()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    units = len(probs) * nrhs
+    value = world * units * args.steps / elapsed
+    _, _, launches = batch.info()
+
+    # error of three problems against exact direct-sum rows (approximation error)
+    from paper_2004_14229_gb300 import direct_rows
+    errs = []
+    for i in range(min(3, len(probs))):
+        p = probs[i]
+        rows = sample_rows(p["targets"].shape[0], 64, seed=11 + i)
+        want = direct_rows(torch.from_numpy(p["targets"]).cuda(), torch.from_numpy(p["sources"]).cuda(),
+                           p["kappa"], torch.from_numpy(p["x"][0]).cuda(), torch.from_numpy(rows).cuda())
+        got = ys[i][0].cpu().numpy()[rows]
+        w = want.cpu().numpy()
+        errs.append(float(np.linalg.norm(got - w) / np.linalg.norm(w)))
+
+    # end to end: pinned host x in, y out, every step
+    xh = [torch.from_numpy(p["x"].astype(np.complex64)).pin_memory() for p in probs]
+    yh = [torch.empty(y.shape, dtype=y.dtype).pin_memory() for y in ys]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for a, b in zip(xs, xh):
+            a.copy_(b, non_blocking=True)
+        batch.apply(xs, ys)
+        for a, b in zip(yh, ys):
+            a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(v.numel() * v.element_size() for v in xh)
+    d2h = sum(v.numel() * v.element_size() for v in yh)
+
+    n = order ** 3
+    flops = sum(8.0 * n * n * st["n_coupling"] for st in stats) * nrhs
+    peaks, src = _peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = flops / (elapsed / args.steps) / 1e12
+    line = {"metric": "RHS-matvecs/s, %d independent problems x %d complex64 RHS (batched form)"
+                      % (len(probs), nrhs),
+            "value": value, "unit": "RHS-matvecs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x3+f32", "data": "synthetic",
+            "config": {"workload": "batch-%d-o5-nrhs16" % len(probs), "problems": len(probs), "nrhs": nrhs,
+                       "order": order, "n_points_total": int(sum(p["targets"].shape[0] for p in probs)),
+                       "root": "bounding dyadic cube", "precision": "tc",
+                       "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2": "inputs larger than L2 (operators of all problems streamed every step)"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_m2l_tc",
+                         "peak_source": "%s sustained bf16; achieved = M2L algorithmic flops / whole step"
+                                        % src},
+            "e2e": {"value": world * units / e2e_s, "unit": "RHS-matvecs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches * args.steps,
+            "setup_s": setup_s, "device_bytes": int(sum(st["device_bytes"] for st in stats)),
+            "rel_err_vs_direct_rows": errs, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,9 +415,12 @@ def main():
     ap.add_argument("--precision", default="tc", choices=["tc", "fp64"])
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch > 0:
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -229,6 +229,60 @@ dfdm_status dfdm_direct_rows_noalloc(const double *targets, int64_t n_t,
 /* Frees the plan and everything it owns; NULL is allowed. */
 dfdm_status dfdm_plan_destroy(dfdm_plan plan);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent products, each of Sect. 2 for its own P_T, P_S and kappa
+ * (the paper treats one problem at a time; the batched form is this
+ * library's).  One plan per problem; dfdm_batch_apply issues every plan's
+ * apply on a set of worker streams, the problems placed largest first on the
+ * least-loaded stream (estimated flops: 8 n^2 N_C + 20 nearfield entries),
+ * and captures all of it once into a CUDA graph; later applies with the same
+ * vector pointers and nrhs replay that graph with one launch. */
+typedef struct {
+  const double *targets; /* HOST, n_t x 3 doubles (copied at create)          */
+  int64_t n_t;
+  const double *sources; /* HOST, n_s x 3 doubles (copied at create)          */
+  int64_t n_s;
+  double kappa;          /* > 0                                               */
+  int max_depth;         /* tree depth of this problem; -1 = params->max_depth */
+} dfdm_problem;
+
+typedef struct dfdm_batch_s *dfdm_batch;
+
+/* Creates one plan per problem with *params (max_depth per problem as
+ * above; params->n_max must be 0: uniform trees).  nstreams worker streams
+ * (0 = 4, at most 64, never more than nprob).  Plans are built one after the
+ * other on `stream`; returns after all are built.  Errors as
+ * dfdm_plan_create (the message names the problem), INVALID_ARG for
+ * nprob < 1 or a bad nstreams, CUDA if a stream or event cannot be made. */
+dfdm_status dfdm_batch_create(int nprob, const dfdm_problem *probs,
+                              const dfdm_params *params, int nstreams,
+                              void *stream, dfdm_batch *out);
+
+/* Applies every problem: y[i] = A_i x[i] for nrhs right-hand sides, x[i]
+ * and y[i] DEVICE pointers laid out as in dfdm_apply.  The graph's launch is
+ * ordered on `stream` (work inside it runs on the batch's own streams, after
+ * everything issued earlier on `stream`, and `stream` waits for all of it).
+ * The first call, or a call whose pointers or nrhs differ from the captured
+ * ones, captures a new graph: that call must not itself be inside a stream
+ * capture.  Errors: INVALID_ARG, CUDA; device-side errors through
+ * dfdm_batch_check. */
+dfdm_status dfdm_batch_apply(dfdm_batch b, void *const *x, void *const *y,
+                             int nrhs, void *stream);
+
+/* dfdm_plan_check on every plan; returns the first error found. */
+dfdm_status dfdm_batch_check(dfdm_batch b, void *stream);
+
+/* Borrows problem i's plan (stats, exports, timing); owned by the batch. */
+dfdm_status dfdm_batch_plan(dfdm_batch b, int i, dfdm_plan *out);
+
+/* Worker stream count, the stream of every problem (nprob ints, may be
+ * NULL) and the kernel launches the captured graph holds (may be NULL). */
+dfdm_status dfdm_batch_info(dfdm_batch b, int *nstreams, int *stream_of,
+                            int64_t *launches);
+
+/* Frees the batch, its graph, streams and plans; NULL is allowed. */
+dfdm_status dfdm_batch_destroy(dfdm_batch b);
+
 /* Description of the last error on this thread (never NULL). */
 const char *dfdm_last_error(void);
 

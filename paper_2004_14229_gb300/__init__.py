@@ -10,7 +10,7 @@ import os
 
 import numpy as np
 
-__all__ = ["DFDMError", "Plan", "load_library", "LIB_PATH", "EXPORTED_SYMBOLS",
+__all__ = ["DFDMError", "Plan", "Batch", "Problem", "Params", "load_library", "LIB_PATH", "EXPORTED_SYMBOLS",
            "FP64", "TC_FP16X3"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdfdm.so")
@@ -26,6 +26,8 @@ EXPORTED_SYMBOLS = [
     "dfdm_plan_check", "dfdm_plan_stats", "dfdm_plan_export_tree",
     "dfdm_plan_export_offsets", "dfdm_plan_destroy", "dfdm_last_error", "dfdm_version",
     "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows", "dfdm_direct_rows_noalloc",
+    "dfdm_batch_create", "dfdm_batch_apply", "dfdm_batch_check", "dfdm_batch_plan",
+    "dfdm_batch_info", "dfdm_batch_destroy",
 ]
 
 
@@ -52,6 +54,11 @@ class Stats(ctypes.Structure):
                 ("n_leaves_t", ctypes.c_int64), ("n_leaves_s", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("level_dirs", ctypes.c_int32 * 16),
                 ("level_coupling", ctypes.c_int64 * 16), ("level_offsets", ctypes.c_int32 * 16)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("targets", ctypes.c_void_p), ("n_t", ctypes.c_int64), ("sources", ctypes.c_void_p),
+                ("n_s", ctypes.c_int64), ("kappa", ctypes.c_double), ("max_depth", ctypes.c_int)]
 
 
 class Timing(ctypes.Structure):
@@ -86,6 +93,13 @@ def load_library():
         "dfdm_direct_rows": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_direct_rows_noalloc": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_plan_timing": [vp, ctypes.POINTER(Timing)],
+        "dfdm_batch_create": [i32, ctypes.POINTER(Problem), ctypes.POINTER(Params), i32, vp,
+                              ctypes.POINTER(vp)],
+        "dfdm_batch_apply": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp],
+        "dfdm_batch_check": [vp, vp],
+        "dfdm_batch_plan": [vp, i32, ctypes.POINTER(vp)],
+        "dfdm_batch_info": [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(i64)],
+        "dfdm_batch_destroy": [vp],
         "dfdm_last_error": [],
         "dfdm_version": [],
     }
@@ -144,6 +158,24 @@ def direct_rows(targets, sources, kappa, x, rows, stream=None, y=None, noalloc=F
     return y
 
 
+def _params(lib, order, max_depth, n_max, eta2, l_hf, root, precision, nrhs_max):
+    p = Params()
+    _check(lib.dfdm_params_default(ctypes.byref(p)))
+    p.order, p.max_depth, p.n_max, p.eta2 = int(order), int(max_depth), int(n_max), float(eta2)
+    p.l_hf = -2 if l_hf is None else int(l_hf)
+    if isinstance(root, str) and root == "bounding":
+        p.root_mode = 1
+    else:
+        lo, side = root
+        p.root_mode = 0
+        for i in range(3):
+            p.root_lo[i] = float(lo[i])
+        p.root_side = float(side)
+    p.precision = int(precision)
+    p.nrhs_max = int(nrhs_max)
+    return p
+
+
 class Plan:
     """A plan of the fast directional product for fixed P_T, P_S and kappa.
 
@@ -160,28 +192,24 @@ class Plan:
         lib = load_library()
         self._lib = lib
         self._h = ctypes.c_void_p(0)
+        self._owned = True
         t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         s = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
-        p = Params()
-        _check(lib.dfdm_params_default(ctypes.byref(p)))
-        p.order, p.max_depth, p.n_max, p.eta2 = int(order), int(max_depth), int(n_max), float(eta2)
-        p.l_hf = -2 if l_hf is None else int(l_hf)
-        if isinstance(root, str) and root == "bounding":
-            p.root_mode = 1
-        else:
-            lo, side = root
-            p.root_mode = 0
-            for i in range(3):
-                p.root_lo[i] = float(lo[i])
-            p.root_side = float(side)
-        p.precision = int(precision)
-        p.nrhs_max = int(nrhs_max)
+        p = _params(lib, order, max_depth, n_max, eta2, l_hf, root, precision, nrhs_max)
         self.precision = int(precision)
         self.n_targets, self.n_sources = t.shape[0], s.shape[0]
         self.nrhs_max = int(nrhs_max)
         _check(lib.dfdm_plan_create(t.ctypes.data, t.shape[0], s.ctypes.data, s.shape[0],
                                     float(kappa), ctypes.byref(p), _stream_handle(stream),
                                     ctypes.byref(self._h)))
+
+    @classmethod
+    def _borrowed(cls, lib, handle, n_targets, n_sources, precision, nrhs_max):
+        self = cls.__new__(cls)
+        self._lib, self._h, self._owned = lib, handle, False
+        self.precision, self.n_targets, self.n_sources = precision, n_targets, n_sources
+        self.nrhs_max = nrhs_max
+        return self
 
     # -------------------------------------------------------------- apply
     @property
@@ -271,9 +299,9 @@ class Plan:
         return off, dirs
 
     def close(self):
-        if self._h:
+        if self._h and self._owned:
             self._lib.dfdm_plan_destroy(self._h)
-            self._h = ctypes.c_void_p(0)
+        self._h = ctypes.c_void_p(0)
 
     def __del__(self):
         try:
@@ -286,3 +314,89 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Independent problems applied together (dfdm_batch_*): one plan each,
+    launches spread over worker streams and replayed from one CUDA graph.
+
+    problems: sequence of dicts with "targets", "sources" ((N, 3) float64
+    host arrays), "kappa" and optionally "max_depth".  The other arguments are
+    shared by all problems, as in Plan (n_max must be 0).
+    """
+
+    def __init__(self, problems, order=5, max_depth=6, eta2=5.0, l_hf=None,
+                 root="bounding", precision=TC_FP16X3, nrhs_max=1, nstreams=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p(0)
+        self._keep = []
+        arr = (Problem * len(problems))()
+        for i, pr in enumerate(problems):
+            t = np.ascontiguousarray(pr["targets"], dtype=np.float64).reshape(-1, 3)
+            s = np.ascontiguousarray(pr["sources"], dtype=np.float64).reshape(-1, 3)
+            self._keep += [t, s]
+            arr[i].targets, arr[i].n_t = t.ctypes.data, t.shape[0]
+            arr[i].sources, arr[i].n_s = s.ctypes.data, s.shape[0]
+            arr[i].kappa = float(pr["kappa"])
+            arr[i].max_depth = int(pr.get("max_depth", -1))
+        p = _params(lib, order, max_depth, 0, eta2, l_hf, root, precision, nrhs_max)
+        _check(lib.dfdm_batch_create(len(problems), arr, ctypes.byref(p), int(nstreams),
+                                     _stream_handle(stream), ctypes.byref(self._h)))
+        self._keep = []
+        self.precision, self.nrhs_max = int(precision), int(nrhs_max)
+        self.plans = []
+        for i, pr in enumerate(problems):
+            h = ctypes.c_void_p(0)
+            _check(lib.dfdm_batch_plan(self._h, i, ctypes.byref(h)))
+            self.plans.append(Plan._borrowed(lib, h, arr[i].n_t, arr[i].n_s, self.precision,
+                                             self.nrhs_max))
+
+    def apply(self, xs, ys, stream=None):
+        """ys[i] = A_i xs[i] for CUDA tensors (torch) of shape (nrhs, n_s_i) /
+        (nrhs, n_t_i), all problems with the same nrhs; ys are overwritten."""
+        import torch
+        tdt = torch.complex128 if self.precision == FP64 else torch.complex64
+        n = len(self.plans)
+        if len(xs) != n or len(ys) != n:
+            raise ValueError("need one x and one y per problem")
+        nrhs = None
+        for i, (x, y, pl) in enumerate(zip(xs, ys, self.plans)):
+            for name, v, m in (("x", x, pl.n_sources), ("y", y, pl.n_targets)):
+                if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == tdt and v.is_contiguous()):
+                    raise TypeError("%s[%d] must be a contiguous CUDA tensor of dtype %s" % (name, i, tdt))
+                if v.shape[-1] != m:
+                    raise ValueError("%s[%d] has %d entries per vector, expected %d" % (name, i, v.shape[-1], m))
+            r = 1 if x.dim() == 1 else x.shape[0]
+            if nrhs is None:
+                nrhs = r
+            if r != nrhs or (1 if y.dim() == 1 else y.shape[0]) != nrhs:
+                raise ValueError("every problem must have the same nrhs")
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        _check(self._lib.dfdm_batch_apply(self._h, xp, yp, int(nrhs), _stream_handle(stream)))
+        return ys
+
+    def check(self, stream=None):
+        _check(self._lib.dfdm_batch_check(self._h, _stream_handle(stream)))
+
+    def info(self):
+        """(worker streams, stream of each problem, launches in the graph)."""
+        ns = ctypes.c_int(0)
+        so = np.zeros(len(self.plans), dtype=np.int32)
+        nl = ctypes.c_int64(0)
+        _check(self._lib.dfdm_batch_info(self._h, ctypes.byref(ns), so.ctypes.data, ctypes.byref(nl)))
+        return ns.value, so, nl.value
+
+    def close(self):
+        if self._h:
+            for pl in self.plans:
+                pl.close()
+            self._lib.dfdm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

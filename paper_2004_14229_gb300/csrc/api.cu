@@ -90,9 +90,6 @@ void bounding_root(const double *t, int64_t nt, const double *s, int64_t ns,
 
 using namespace dfdm;
 
-struct dfdm_plan_s {
-  Plan p;
-};
 
 extern "C" {
 

@@ -240,3 +240,8 @@ void apply_fp64(Plan &plan, const double2 *x, double2 *y, int nrhs,
                 cudaStream_t st);
 
 }  // namespace dfdm
+
+// The opaque handle of include/dfdm.h.
+struct dfdm_plan_s {
+  dfdm::Plan p;
+};

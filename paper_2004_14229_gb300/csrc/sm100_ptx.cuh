@@ -87,6 +87,14 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
 }
 // Multicast variant: the tile lands at the same CTA-relative offset in every
 // CTA of `mask` in the cluster and signals each one's mbarrier at `bar`'s offset.
+// Untiled bulk copy global -> this CTA's shared memory, completion counted
+// on `bar` in bytes.  dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
                                                int c2, uint16_t mask) {
   asm volatile(

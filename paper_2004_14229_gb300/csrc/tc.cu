@@ -79,9 +79,20 @@ __device__ __forceinline__ void atomic_max_abs(float *addr, float v) {
 // Real-stacked coupling operator of (level, d), scaled by 2^e and split:
 // row j < n: [Re A[j, :], -Im A[j, :]]; row NH + j: [Im A[j, :], Re A[j, :]],
 // with NH = NP / 2 the half of the padded output rows.
+// Operator image: for each (op, output half h, K step kc) one contiguous
+// block [hi | lo], each NH rows x 16 halves (32 B) in the 32-byte swizzled
+// layout the MMA descriptors read (16-byte chunk index XOR bit 2 of the row),
+// so one untiled bulk copy moves a whole stage's operator half.
+__device__ __forceinline__ int64_t op_image_index(int64_t op, int h, int kc, int hl, int j, int e, int KSTEPS,
+                                                  int NH) {
+  const int chunk = (e >> 3) ^ ((j >> 2) & 1);
+  const int64_t tile = ((op * 2 + h) * KSTEPS + kc) * 2 + hl;
+  return tile * NH * 16 + j * 16 + chunk * 8 + (e & 7);
+}
+
 __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t *op_level,
                                  const int32_t *op_off, const double *op_dir, const double *level_w,
-                                 const float *level_scale, double kappa, __half *ohi, __half *olo) {
+                                 const float *level_scale, double kappa, __half *opk) {
   const int op = blockIdx.y;
   const int row = blockIdx.x;  // 0 .. 2 NH - 1
   const int l = op_level[op];
@@ -89,8 +100,7 @@ __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t
   const float sc = level_scale[l];
   const bool im_row = row >= NH;
   const int j = im_row ? row - NH : row;
-  __half *dhi = ohi + ((int64_t)op * 2 * NH + row) * KP;
-  __half *dlo = olo + ((int64_t)op * 2 * NH + row) * KP;
+  const int KSTEPS = KP / 16;
   const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
   const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
   for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
@@ -118,8 +128,9 @@ __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t
     }
     const __half hi = __float2half_rn(val);
     const __half lo = __float2half_rn(val - __half2float(hi));
-    dhi[kk] = hi;
-    dlo[kk] = lo;
+    const int kc = kk >> 4, e = kk & 15, hh = im_row ? 1 : 0;
+    opk[op_image_index(op, hh, kc, 0, j, e, KSTEPS, NH)] = hi;
+    opk[op_image_index(op, hh, kc, 1, j, e, KSTEPS, NH)] = lo;
   }
 }
 
@@ -392,25 +403,28 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
 
 // ------------------------------------------------------------- M2L (TC)
 // One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
-// grid), all NP stacked outputs, one level.  The outputs form two halves of
-// NH = NP / 2 columns (two TMEM regions).  Per K step of 16 and half h:
-//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[h]
-//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[h]
-// so TMEM lanes 0..63 of region h hold H = M_hi O_hi and lanes 64..127 the
-// cross terms X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one
-// smem buffer [Z | M_hi | M_lo]).  The tensor core truncates its FP32
-// accumulator towards zero after every instruction, so H never accumulates
-// more than KSTEPS / kKsplit instructions: the MMAs of one operator run as
-// work units (K part, half), and after each unit four epilogue warps add
-// that region's H to an FP32 shared-memory sum R (round to nearest) and
-// clear it, while the MMAs already fill the other region.  X is 2^-11 of H;
-// it is added to R every kFlushOps operators and when the direction slot
-// changes, and R then goes to the FP32 local grid.
+// grid), one level.  The NP stacked outputs are computed in two passes, one
+// per half of NH = NP / 2 rows (first the real parts, then the imaginary
+// parts).  Per K step of 16:
+//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[half]
+//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[half]
+// so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 the cross terms
+// X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one smem buffer
+// [Z | M_hi | M_lo]).  The tensor core truncates its FP32 accumulator
+// towards zero after every instruction, so H never accumulates more than
+// KSTEPS / kKsplit instructions: each operator runs as kKsplit work units
+// (K parts) that alternate between two TMEM regions, and after each unit
+// eight epilogue warps add that region's H to an FP32 shared-memory sum R
+// (round to nearest) and clear it while the MMAs fill the other region.
+// X is 2^-11 of H; it is added to R every kFlushOps operators and when the
+// direction slot changes, and R then goes to the FP32 local grid.  Holding
+// R for one half only leaves room for 8 pipeline stages at order 6.
 struct M2lArgs {
   const int32_t *alpha_ops;   // level's op list (global op indices), per alpha
   const int32_t *alpha_off;   // 9 offsets into alpha_ops
   const int32_t *op_off;      // 3 ints per global op
   const int32_t *op_slot;     // slot per global op
+  const __half *opk;          // operator images of the level (first op = op_base)
   int op_base;                // first global op of the level
   float *loc;                 // FP32 locals [slot][cell][KP]
   int g;                      // level grid
@@ -418,17 +432,19 @@ struct M2lArgs {
   int KP;                     // padded stacked length (= NP)
   const int *mom_exp;         // moment scale exponent of the level (device)
   int op_exp;                 // operator scale exponent of the level
+  int nsplit;                 // CTAs per (tile, alpha), each a contiguous chunk of the op list
   int *err;                   // error word
 };
 
 constexpr int kTM = 64;                   // targets per CTA
 constexpr int kTX = 4, kTY = 4, kTZ = 4;  // parent-grid block of a CTA
 constexpr int kK = 16;                    // K per stage (32-byte rows)
-constexpr int kSt = 5;                    // pipeline stages
-constexpr int kKsplit = 2;                // K parts per operator (units per half)
-constexpr int kM2lWarps = 18;             // 0 TMA, 1 MMA, 2-3 X drain, 8 H warps
+constexpr int kKsplit = 2;                // K parts (work units) per operator and half
+constexpr int kM2lWarps = 16;             // 8 H warps, 6 X warps, 6 TMA, 7 MMA
+constexpr int kTmaWarp = 6, kMmaWarp = 7;
 constexpr int kM2lThreads = kM2lWarps * 32;
-constexpr int kEpiWarps = 10;
+constexpr int kEpiWarps = 14;
+constexpr int kRS = kTM + 1;              // row stride of R (conflict-free both ways)
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kFlushOps = 32;
@@ -443,17 +459,30 @@ struct M2lSmem {
   static constexpr int kOffMhi = kZ, kOffMlo = kZ + kM, kOffOhi = kZ + 2 * kM, kOffOlo = kZ + 2 * kM + kO;
   static constexpr int kStage = kZ + 2 * kM + 2 * kO;
   static constexpr int kTx = 2 * kM + 2 * kO;          // bytes TMA brings per stage
-  static constexpr int kR = kTM * NP * 4;              // FP32 running sums R[col][row]
+  static constexpr int kR = kRS * NH * 4;              // FP32 running sums R[col][row] of one half
+  static constexpr int kStFit = (227 * 1024 - 2048 - kR) / kStage;
+  static constexpr int kSt = kStFit < 12 ? kStFit : 12;
   static constexpr int kTotal = kSt * kStage + kR + 1024;
   static_assert(kStage % 1024 == 0, "stage alignment");
+  static_assert(kOffOlo == kOffOhi + kO, "operator hi and lo tiles are one contiguous copy");
+  static_assert(kSt >= 3, "too few pipeline stages");
 };
 
-// H warps: 4, 5, 8, 9 (region 0) and 12, 13, 16, 17 (region 1); lane
-// quarter q = warp & 3 in {0, 1}, column group g in {0, 1} of the region.
+// H warps: 0, 1, 4, 5, 8, 9, 12, 13; lane quarter q = warp & 3 in {0, 1},
+// column group hi >> 1 in {0, 1, 2, 3}.  Every H warp drains every unit (both
+// TMEM regions), so each element of R has exactly one writer.  (A warp reaches
+// TMEM lanes 32 (warp % 4) ... + 31 only.)  Sixteen warps, four per SM
+// sub-partition, leave 128 registers a thread.
 __device__ __forceinline__ int h_index(int warp) {
+  return ((warp & 3) < 2 && warp < 14) ? ((warp >> 2) << 1) | (warp & 1) : -1;
+}
+// X warps: 2, 3, 10, 11, 14, 15 (lane quarters 2, 3: the cross terms of
+// targets 0..31 and 32..63); column group 0, 1, 2 of three.
+__device__ __forceinline__ int x_index(int warp) {
   switch (warp) {
-    case 4: return 0; case 5: return 1; case 8: return 2; case 9: return 3;
-    case 12: return 4; case 13: return 5; case 16: return 6; case 17: return 7;
+    case 2: case 3: return 0;
+    case 10: case 11: return 1;
+    case 14: case 15: return 2;
     default: return -1;
   }
 }
@@ -461,21 +490,19 @@ __device__ __forceinline__ int h_index(int warp) {
 template <int NP>
 __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant__ CUtensorMap map_mhi,
                                                           const __grid_constant__ CUtensorMap map_mlo,
-                                                          const __grid_constant__ CUtensorMap map_ohi,
-                                                          const __grid_constant__ CUtensorMap map_olo,
                                                           const M2lArgs args) {
   using S = M2lSmem<NP>;
   constexpr int NH = NP / 2;               // N of one MMA (<= 256)
   constexpr int KSTEPS = NP / kK;          // K steps per operator (KP == NP)
   constexpr int USTEPS = KSTEPS / kKsplit; // K steps per unit
-  constexpr int GCOLS = NH / 2;            // columns per H warp
+  constexpr int NCH = NH / 16;             // 16-column chunks of a half
+  constexpr int kSt = S::kSt;
   constexpr uint32_t kTmemCols = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
   static_assert(NH % 16 == 0 && NH <= 256, "N half must be a multiple of 16, <= 256");
-  static_assert(GCOLS % 16 == 0, "H warp column group must be a multiple of 16");
   static_assert(KSTEPS % kKsplit == 0, "K steps must split evenly");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NP][kTM]
+  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NH][kTM]
   __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full[2], acc_empty[2], grp_done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
@@ -489,28 +516,32 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   const int Y0 = ((tile / tiles_x) % tiles_y) * kTY;
   const int Z0 = (tile / (tiles_x * tiles_y)) * kTZ;
   const int ax = alpha & 1, ay = (alpha >> 1) & 1, az = (alpha >> 2) & 1;
-  const int i0 = args.alpha_off[alpha], i1 = args.alpha_off[alpha + 1];
+  // this CTA's chunk of the alpha's operator list (blockIdx.z of nsplit)
+  const int a0 = args.alpha_off[alpha], na = args.alpha_off[alpha + 1] - a0;
+  const int i0 = a0 + (int)(((int64_t)na * blockIdx.z) / args.nsplit);
+  const int i1 = a0 + (int)(((int64_t)na * (blockIdx.z + 1)) / args.nsplit);
+  const bool shared_out = args.nsplit > 1;   // other CTAs add to the same locals
 
   // zero rows of every stage and the running sums
   for (int s = 0; s < kSt; ++s)
     for (int i = tid; i < S::kZ / 16; i += blockDim.x)
       reinterpret_cast<uint4 *>(smem + s * S::kStage)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < kTM * NP; i += blockDim.x) R[i] = 0.f;
+  for (int i = tid; i < kRS * NH; i += blockDim.x) R[i] = 0.f;
   ptx::fence_proxy_async();
   if (tid == 0) {
     for (int s = 0; s < kSt; ++s) {
       ptx::mbar_init(&full_bar[s], 1);
       ptx::mbar_init(&empty_bar[s], 1);
     }
-    for (int h = 0; h < 2; ++h) {
-      ptx::mbar_init(&acc_full[h], 1);
-      ptx::mbar_init(&acc_empty[h], 4);
+    for (int r = 0; r < 2; ++r) {
+      ptx::mbar_init(&acc_full[r], 1);
+      ptx::mbar_init(&acc_empty[r], 8);
     }
     ptx::mbar_init(&grp_done, kEpiWarps);
     s_abort = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     ptx::tmem_alloc(&tmem_base, kTmemCols);
     ptx::tmem_relinquish();
   }
@@ -519,26 +550,22 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   ptx::tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0) {
+  if (warp == kTmaWarp) {
     if (lane == 0) {
       // ------------------------------------------------ TMA producer
       ptx::prefetch_tensormap(&map_mhi);
       ptx::prefetch_tensormap(&map_mlo);
-      ptx::prefetch_tensormap(&map_ohi);
-      ptx::prefetch_tensormap(&map_olo);
       uint32_t it = 0;
       bool ok = true;
-      for (int ii = i0; ii < i1 && ok; ++ii) {
-        const int op = args.alpha_ops[ii];
-        const int slot = args.op_slot[op];
-        const int x0 = 2 * X0 + ax - args.op_off[3 * op];
-        const int y0 = 2 * Y0 + ay - args.op_off[3 * op + 1];
-        const int z0 = 2 * Z0 + az - args.op_off[3 * op + 2];
-        const int opl = op - args.op_base;
-        for (int u = 0; u < 2 * kKsplit && ok; ++u) {
-          const int kh = u >> 1, h = u & 1;
-          for (int ks = 0; ks < USTEPS; ++ks, ++it) {
-            const int kc = kh * USTEPS + ks;
+      for (int h = 0; h < 2 && ok; ++h) {
+        for (int ii = i0; ii < i1 && ok; ++ii) {
+          const int op = args.alpha_ops[ii];
+          const int slot = args.op_slot[op];
+          const int x0 = 2 * X0 + ax - args.op_off[3 * op];
+          const int y0 = 2 * Y0 + ay - args.op_off[3 * op + 1];
+          const int z0 = 2 * Z0 + az - args.op_off[3 * op + 2];
+          const int opl = op - args.op_base;
+          for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
             const int st = it % kSt;
             const uint32_t ph = (it / kSt) & 1;
             if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
@@ -546,8 +573,8 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
             ptx::mbar_expect_tx(&full_bar[st], S::kTx);
             ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
             ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
-            ptx::tma_load_3d(base + S::kOffOhi, &map_ohi, &full_bar[st], kc * kK, h * NH, opl);
-            ptx::tma_load_3d(base + S::kOffOlo, &map_olo, &full_bar[st], kc * kK, h * NH, opl);
+            ptx::bulk_load(base + S::kOffOhi, args.opk + (((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 * NH * 16,
+                           2 * S::kO, &full_bar[st]);
           }
         }
       }
@@ -556,49 +583,51 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
         atomicExch(&s_abort, 1);
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
       constexpr uint32_t idesc = ptx::idesc_f16_f32(128, NH);
       uint32_t it = 0, groups = 0;
-      uint32_t units[2] = {0, 0};   // units issued per region
+      uint32_t units[2] = {0, 0};   // units issued per TMEM region
       bool ok = true;
-      int run = 0;
-      for (int ii = i0; ii < i1 && ok; ++ii) {
-        const int slot = args.op_slot[args.alpha_ops[ii]];
-        const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
-        for (int u = 0; u < 2 * kKsplit && ok; ++u) {
-          const int h = u & 1;
-          if (units[h] > 0) {   // region drained by the epilogue?
-            if (!ptx::mbar_wait(&acc_empty[h], (units[h] - 1) & 1, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
-          }
-          const uint32_t d = tmem + h * NH;
-          for (int ks = 0; ks < USTEPS; ++ks, ++it) {
-            const int st = it % kSt;
-            const uint32_t ph = (it / kSt) & 1;
-            if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
-            const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
-            const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
-            const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
-            const uint32_t init = (units[h] == 0 && ks == 0) ? 0u : 1u;
-            ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi), idesc, init);
-            ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo), idesc, 1u);
-            ptx::mma_commit(&empty_bar[st]);
+      for (int h = 0; h < 2 && ok; ++h) {
+        int run = 0;
+        for (int ii = i0; ii < i1 && ok; ++ii) {
+          const int slot = args.op_slot[args.alpha_ops[ii]];
+          const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
+          for (int u = 0; u < kKsplit && ok; ++u) {
+            const int r = u & 1;       // TMEM region of this unit
+            if (units[r] > 0) {        // region drained by the epilogue?
+              if (!ptx::mbar_wait(&acc_empty[r], (units[r] - 1) & 1, kWaitLimit)) { ok = false; break; }
+              ptx::tc_fence_after();
+            }
+            const uint32_t d = tmem + r * NH;
+            for (int ks = 0; ks < USTEPS; ++ks, ++it) {
+              const int st = it % kSt;
+              const uint32_t ph = (it / kSt) & 1;
+              if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
+              ptx::tc_fence_after();
+              const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
+              const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
+              const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
+              const uint32_t init = (units[r] == 0 && ks == 0) ? 0u : 1u;
+              ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi), idesc, init);
+              ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo), idesc, 1u);
+              ptx::mma_commit(&empty_bar[st]);
+            }
+            if (!ok) break;
+            ptx::mma_commit(&acc_full[r]);
+            ++units[r];
           }
           if (!ok) break;
-          ptx::mma_commit(&acc_full[h]);
-          ++units[h];
-        }
-        if (!ok) break;
-        ++run;
-        if (next_slot != slot || run >= kFlushOps) {
-          // X and R are drained after this operator: wait for the epilogue
-          if (!ptx::mbar_wait(&grp_done, groups & 1, kWaitLimit)) { ok = false; break; }
-          ptx::tc_fence_after();
-          ++groups;
-          run = 0;
+          ++run;
+          if (next_slot != slot || run >= kFlushOps) {
+            // X and R are drained after this operator: wait for the epilogue
+            if (!ptx::mbar_wait(&grp_done, groups & 1, kWaitLimit)) { ok = false; break; }
+            ptx::tc_fence_after();
+            ++groups;
+            run = 0;
+          }
         }
       }
       if (!ok) {
@@ -609,153 +638,194 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   } else {
     // ------------------------------------------------ epilogue
     const int hi = h_index(warp);
-    const bool xw = (warp == 2 || warp == 3);
+    const int xi = x_index(warp);
+    const bool xw = xi >= 0;
     if (hi >= 0 || xw) {
       const int q = warp & 3;                        // TMEM lane quarter
       const int r = (q & 1) * 32 + lane;             // target row 0..63
-      const int ix = r % kTX, iy = (r / kTX) % kTY, iz = r / (kTX * kTY);
-      const int X = X0 + ix, Y = Y0 + iy, Z = Z0 + iz;
-      const bool valid = X < gp && Y < gp && Z < gp;
-      const int64_t cell = (2 * X + ax) + (int64_t)g * ((2 * Y + ay) + (int64_t)g * (2 * Z + az));
       const int64_t ncell = (int64_t)g * g * g;
       const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
       const int n = args.n;
       const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-      const int region = (hi >= 0) ? hi / 4 : -1;
-      const int c0 = (hi >= 0) ? region * NH + ((hi >> 1) & 1) * GCOLS : 0;   // first column of this H warp
+      const int gq = (hi >= 0) ? hi >> 1 : 0;   // column group of this H warp
       const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      uint32_t drains = 0;   // units of this warp's region drained so far
-      int run = 0;
+      uint32_t drains[2] = {0, 0};   // units drained so far, per TMEM region
       bool stop = false;
-      for (int ii = i0; ii < i1 && !stop; ++ii) {
-        const int slot = args.op_slot[args.alpha_ops[ii]];
-        const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
-        ++run;
-        const bool group_end = (next_slot != slot) || run >= kFlushOps;
-        bool bad = false;
-        if (hi >= 0) {
-          for (int u = 0; u < kKsplit && !bad; ++u, ++drains) {
-            bool got = false;
-            const uint64_t t0 = ptx::global_ns();
-            for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
-              got = ptx::mbar_try_wait(&acc_full[region], drains & 1);
-              if (!got && (t & 255) == 255 &&
-                  (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
-                break;
-            }
-            if (!got) { bad = true; break; }
-            ptx::tc_fence_after();
+      for (int h = 0; h < 2 && !stop; ++h) {
+        int run = 0;
+        for (int ii = i0; ii < i1 && !stop; ++ii) {
+          const int slot = args.op_slot[args.alpha_ops[ii]];
+          const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
+          ++run;
+          const bool group_end = (next_slot != slot) || run >= kFlushOps;
+          bool bad = false;
+          if (hi >= 0) {
+            // unit u of this operator went to TMEM region u & 1
+            for (int u = 0; u < kKsplit && !bad; ++u) {
+              const int reg = u & 1;
+              bool got = false;
+              const uint64_t t0 = ptx::global_ns();
+              for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
+                got = ptx::mbar_try_wait(&acc_full[reg], drains[reg] & 1);
+                if (!got && (t & 255) == 255 &&
+                    (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
+                  break;
+              }
+              if (!got) { bad = true; break; }
+              ++drains[reg];
+              ptx::tc_fence_after();
 #pragma unroll 1
-            for (int c = c0; c < c0 + GCOLS; c += 16) {
-              float v[16];
-              ptx::tmem_ld16(tmem + lane_addr + c, v);
-              ptx::tmem_ld_wait();
+              for (int ch = gq; ch < NCH; ch += 4) {
+                const int c = ch * 16;
+                float v[16];
+                ptx::tmem_ld16(tmem + lane_addr + reg * NH + c, v);
+                ptx::tmem_ld_wait();
 #pragma unroll
-              for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
-              ptx::tmem_st16(tmem + lane_addr + c, zero);
+                for (int i = 0; i < 16; ++i) R[(c + i) * kRS + r] += v[i];
+                ptx::tmem_st16(tmem + lane_addr + reg * NH + c, zero);
+              }
+              ptx::tmem_st_wait();
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive(&acc_empty[reg]);
             }
-            ptx::tmem_st_wait();
+          }
+          if (bad) atomicExch(args.err, 1);
+          // one decision for all epilogue warps; it also orders this
+          // operator's H drains before the X drain below
+          stop = ptx::named_bar_or(2, kEpiThreads, bad || *(volatile int *)&s_abort);
+          if (stop) break;
+          if (group_end) {
+            if (xw) {
+              // X of both regions -> R, then clear X (every unit of this
+              // operator has completed: the H warps consumed all acc_full)
+              ptx::tc_fence_after();
+#pragma unroll 1
+              for (int ch = xi; ch < NCH; ch += 3) {
+                const int c = ch * 16;
+                float v0[16], v1[16];
+                ptx::tmem_ld16(tmem + lane_addr + c, v0);
+                ptx::tmem_ld16(tmem + lane_addr + NH + c, v1);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) R[(c + i) * kRS + r] += v0[i] + v1[i];
+                ptx::tmem_st16(tmem + lane_addr + c, zero);
+                ptx::tmem_st16(tmem + lane_addr + NH + c, zero);
+              }
+              ptx::tmem_st_wait();
+            }
+            ptx::named_bar(1, kEpiThreads);
+            if (hi >= 0) {
+              // R -> local grid (scaled), then clear R: H warp hi takes the
+              // targets rr = hi, hi + 8, ..., its lanes consecutive columns,
+              // so every update of the local grid is one coalesced row.
+#pragma unroll 1
+              for (int rr = hi; rr < kTM; rr += 8) {
+                const int jx = rr % kTX, jy = (rr / kTX) % kTY, jz = rr / (kTX * kTY);
+                const int XX = X0 + jx, YY = Y0 + jy, ZZ = Z0 + jz;
+                const bool ok_r = XX < gp && YY < gp && ZZ < gp;
+                const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
+                float *dst = args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n;
+#pragma unroll
+                for (int j = 0; j < (NH + 31) / 32; ++j) {
+                  const int c = lane + 32 * j;
+                  if (c < NH) {
+                    const float val = R[c * kRS + rr];
+                    R[c * kRS + rr] = 0.f;
+                    if (ok_r && c < n) {
+                      if (shared_out) atomicAdd(dst + c, val * inv);
+                      else dst[c] += val * inv;
+                    }
+                  }
+                }
+              }
+            }
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&acc_empty[region]);
+            if (lane == 0) ptx::mbar_arrive(&grp_done);
+            run = 0;
           }
-        }
-        if (bad) atomicExch(args.err, 1);
-        // one decision for all epilogue warps
-        stop = ptx::named_bar_or(2, kEpiThreads, bad || *(volatile int *)&s_abort);
-        if (stop) break;
-        if (group_end) {
-          if (xw) {
-            // X -> R for both regions, then clear X (every unit of this
-            // operator has completed: the H warps consumed all acc_full)
-            ptx::tc_fence_after();
-#pragma unroll 1
-            for (int c = 0; c < NP; c += 16) {
-              float v[16];
-              ptx::tmem_ld16(tmem + lane_addr + c, v);
-              ptx::tmem_ld_wait();
-#pragma unroll
-              for (int i = 0; i < 16; ++i) R[(c + i) * kTM + r] += v[i];
-              ptx::tmem_st16(tmem + lane_addr + c, zero);
-            }
-            ptx::tmem_st_wait();
-          }
-          ptx::named_bar(1, kEpiThreads);
-          if (hi >= 0) {
-            // R -> local grid (scaled), then clear R; this warp owns rows of
-            // quarter q and columns [c0, c0 + GCOLS) of region `region`
-            float *dst = args.loc + ((int64_t)slot * ncell + cell) * args.KP;
-#pragma unroll 1
-            for (int c = c0; c < c0 + GCOLS; ++c) {
-              const int jj = (c < NH) ? c : c - NH;
-              const float val = R[c * kTM + r];
-              R[c * kTM + r] = 0.f;
-              if (valid && jj < n) dst[(c < NH) ? jj : n + jj] += val * inv;
-            }
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&grp_done);
-          run = 0;
         }
       }
     }
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 1) ptx::tmem_dealloc(tmem, kTmemCols);
+  if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ----------------------------------------------------------------- L2T
+// Knuth's TwoSum: s + t = u + err exactly in round-to-nearest; the rounding
+// errors of a running sum are collected in c (compensated summation).
+__device__ __forceinline__ void two_sum_acc(float &s, float t, float &c) {
+  const float u = __fadd_rn(s, t);
+  const float bp = __fsub_rn(u, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(u, bp)), __fsub_rn(t, bp)));
+  s = u;
+}
+
+// One block per leaf, one thread per target point.  The leaf's local
+// coefficients of one direction slot are staged in shared memory (read as
+// broadcasts); each point's n-term sum uses FP32 products and a compensated
+// FP32 sum (the plain FP32 sum would lose ~sqrt(n) roundings to cancellation),
+// then the slot's plane wave exp(i kappa <x - m_t, c>) with an FP64 argument.
 template <int O>
 __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
                                                  const int32_t *leaf_begin, const int32_t *leaf_end, double w,
                                                  const double *dir, int nslots, double kappa, const float *loc,
                                                  int64_t ncell, int KP, float2 *ysorted) {
-  // Products in FP32, the n-term sum in FP64 (its cancellation would cost
-  // ~sqrt(n) FP32 roundings relative to the result otherwise).
   constexpr int N = O * O * O;
-  __shared__ double2 red[4];
+  __shared__ float g[2 * N];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const float inv_h = (float)(2.0 / w);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
-  for (int p = b; p < e; ++p) {
-    const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
+  for (int p0 = b; p0 < e; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const bool act = p < e;
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
     float lx[O], ly[O], lz[O];
+    if (act) {
+      y0 = lxyz[p];
+      y1 = lxyz[n_pts + p];
+      y2 = lxyz[2 * n_pts + p];
+    }
     lagrange1f<O>(y0 * inv_h, lx);
     lagrange1f<O>(y1 * inv_h, ly);
     lagrange1f<O>(y2 * inv_h, lz);
     double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
       const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
-      double sr = 0.0, si = 0.0;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const int kx = k % O, ky = (k / O) % O, kz = k / (O * O);
-        const float l = lx[kx] * ly[ky] * lz[kz];
-        sr += (double)(l * src[k]);
-        si += (double)(l * src[N + k]);
+      __syncthreads();
+      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = src[i];
+      __syncthreads();
+      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll
+      for (int kz = 0; kz < O; ++kz) {
+#pragma unroll
+        for (int ky = 0; ky < O; ++ky) {
+          const float lyz = ly[ky] * lz[kz];
+          const int k0 = O * (ky + O * kz);
+#pragma unroll
+          for (int kx = 0; kx < O; ++kx) {
+            const float l = lx[kx] * lyz;
+            two_sum_acc(sr, __fmul_rn(l, g[k0 + kx]), cr);
+            two_sum_acc(si, __fmul_rn(l, g[N + k0 + kx]), ci);
+          }
+        }
       }
-      const float2 ph = cexpi_reduced(kappa * ((double)y0 * dir[3 * slot] + (double)y1 * dir[3 * slot + 1] +
-                                               (double)y2 * dir[3 * slot + 2]));
-      tx += sr * ph.x - si * ph.y;
-      ty += sr * ph.y + si * ph.x;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      tx += __shfl_down_sync(0xffffffffu, tx, o);
-      ty += __shfl_down_sync(0xffffffffu, ty, o);
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(tx, ty);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double2 r = red[0];
-      for (int i = 1; i < 4; ++i) {
-        r.x += red[i].x;
-        r.y += red[i].y;
+      const double re = (double)sr + (double)cr, im = (double)si + (double)ci;
+      const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
+      if (c0 == 0.0 && c1 == 0.0 && c2 == 0.0) {
+        tx += re;
+        ty += im;
+      } else {
+        const float2 ph = cexpi_reduced(kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
+        tx += re * ph.x - im * ph.y;
+        ty += re * ph.y + im * ph.x;
       }
-      ysorted[p] = make_float2((float)r.x, (float)r.y);
     }
-    __syncthreads();
+    if (act) ysorted[p] = make_float2((float)tx, (float)ty);
   }
 }
 
@@ -846,6 +916,80 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
   }
 }
 
+// Nearfield for small leaves (at most kSmallLeaf points): one warp per
+// target leaf, lane i takes nearfield offsets i, i + 32, ... and sums that
+// leaf's sources into every target of the leaf; the warp then reduces per
+// target.  Keeps all lanes busy when leaves hold a few points.
+constexpr int kSmallLeaf = 16;
+
+__global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, const int32_t *tperm,
+                                                   const int32_t *leaf_cell, const int32_t *leaf_begin,
+                                                   const int32_t *leaf_end, int64_t nleaves, const float *sl,
+                                                   int64_t ns, const int32_t *sperm, const int32_t *s_leaf_of_cell,
+                                                   const int32_t *sb, const int32_t *se, int g, float w,
+                                                   const int32_t *near_off, int nnear, float kappa,
+                                                   const float2 *x, const float2 *ysorted, float2 *y) {
+  const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (leaf >= nleaves) return;
+  const int cell = leaf_cell[leaf];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const int b = leaf_begin[leaf];
+  const int cnt = min(kSmallLeaf, leaf_end[leaf] - b);
+  const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  float px[kSmallLeaf], py[kSmallLeaf], pz[kSmallLeaf], cr[kSmallLeaf], ci[kSmallLeaf];
+#pragma unroll
+  for (int u = 0; u < kSmallLeaf; ++u) {
+    const bool a = u < cnt;
+    px[u] = a ? tl[b + u] : 0.f;
+    py[u] = a ? tl[nt + b + u] : 0.f;
+    pz[u] = a ? tl[2 * nt + b + u] : 0.f;
+    cr[u] = ci[u] = 0.f;
+  }
+  for (int i = lane; i < nnear; i += 32) {
+    const int dx = near_off[3 * i], dy = near_off[3 * i + 1], dz = near_off[3 * i + 2];
+    const int sx = cx - dx, sy = cy - dy, sz = cz - dz;
+    if (sx < 0 || sy < 0 || sz < 0 || sx >= g || sy >= g || sz >= g) continue;
+    const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
+    if (s < 0) continue;
+    const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
+    for (int q = sb[s]; q < se[s]; ++q) {
+      const float qx = sl[q] - ox, qy = sl[ns + q] - oy, qz = sl[2 * ns + q] - oz;
+      const float2 v = x[sperm[q]];
+#pragma unroll
+      for (int u = 0; u < kSmallLeaf; ++u) {
+        if (u >= cnt) break;
+        const float d0 = px[u] - qx, d1 = py[u] - qy, d2 = pz[u] - qz;
+        const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        if (r2 == 0.f) continue;   // coincident points (zero diagonal)
+        const float ir = rsqrtf(r2);
+        float sn, cs;
+        sincosf(kappa * (r2 * ir), &sn, &cs);
+        const float sc = inv4pi * ir;
+        cr[u] = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr[u]);
+        ci[u] = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kSmallLeaf; ++u) {
+    for (int o = 16; o > 0; o >>= 1) {
+      cr[u] += __shfl_xor_sync(0xffffffffu, cr[u], o);
+      ci[u] += __shfl_xor_sync(0xffffffffu, ci[u], o);
+    }
+  }
+  if (lane < cnt) {
+    // lane u writes target u (registers indexed by a compile-time loop)
+#pragma unroll
+    for (int u = 0; u < kSmallLeaf; ++u) {
+      if (u == lane) {
+        const float2 f = ysorted[b + u];
+        y[tperm[b + u]] = make_float2(cr[u] + f.x, ci[u] + f.y);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -874,8 +1018,8 @@ struct TcState {
   int KP = 0;                            // = NP, padded stacked length
   std::vector<float *> mom32, loc32;     // per level FP32 grids
   std::vector<__half *> mhi, mlo;        // per level split moments
-  std::vector<CUtensorMap> map_mhi, map_mlo, map_ohi, map_olo;
-  __half *ohi = nullptr, *olo = nullptr; // split operators [op][NP][KP]
+  std::vector<CUtensorMap> map_mhi, map_mlo;
+  __half *opk = nullptr;                 // split operator images (see op_image_index)
   std::vector<int> op_exp;               // per level operator scale exponent
   float *maxabs = nullptr;               // per level max |moment|
   int *mom_exp = nullptr;                // per level moment exponent
@@ -883,7 +1027,23 @@ struct TcState {
   float2 *phase = nullptr;               // FP32 directional diagonals
   float *tl = nullptr, *sl = nullptr;    // leaf-local coordinates
   float2 *ysorted = nullptr;
+  int num_sms = 1;
 };
+
+// CTAs per (tile, alpha) for one M2L level: with one resident CTA per SM a
+// level of `ctas` CTAs runs in ceil(ctas / num_sms) waves, so a level with
+// few tiles (the coarse levels) leaves SMs idle.  Splitting every operator
+// list into s chunks costs one more flush per chunk; take the smallest s whose
+// waves per unit of work are within 2 % of the best, keeping >= 16 ops a chunk.
+static int m2l_split(int ctas, int ops_per_alpha, int num_sms) {
+  auto cost = [&](int s) { return (double)(((int64_t)ctas * s + num_sms - 1) / num_sms) / s; };
+  int smax = std::max(1, std::min(32, ops_per_alpha / 16));
+  double best = cost(1);
+  for (int s = 2; s <= smax; ++s) best = std::min(best, cost(s));
+  for (int s = 1; s <= smax; ++s)
+    if (cost(s) <= best * 1.02) return s;
+  return 1;
+}
 
 static TcState &tc_state(Plan &plan) {
   if (!plan.tc) plan.tc = new TcState();
@@ -899,9 +1059,23 @@ void build_tc(Plan &plan, cudaStream_t st) {
   TcState &T = tc_state(plan);
   const int o = plan.order, n = plan.n, p = plan.depth;
   if (o > 7) throw Error{DFDM_ERR_UNSUPPORTED, "tensor-core form supports orders 2..7"};
+  {
+    int dev = 0;
+    DFDM_CUDA_TRY(cudaGetDevice(&dev));
+    DFDM_CUDA_TRY(cudaDeviceGetAttribute(&T.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   const int KP = round_up(2 * n, 64);  // stacked length: N halves and H-drain groups of 16
   if (KP / 2 > 256) throw Error{DFDM_ERR_UNSUPPORTED, "order too large for one MMA N half"};
   T.KP = KP;
+  // opt the M2L kernel into its dynamic shared memory once, here, so the
+  // apply itself makes no attribute calls (it can be captured in a graph)
+  switch (KP) {
+    case 64: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<64>::kTotal)); break;
+    case 128: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<128>::kTotal)); break;
+    case 256: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<256>::kTotal)); break;
+    case 448: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<448>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<448>::kTotal)); break;
+    default: break;
+  }
   // FP32 constants
   {
     double cheb[kMaxOrder] = {0}, lagw[kMaxOrder] = {0};
@@ -970,8 +1144,6 @@ void build_tc(Plan &plan, cudaStream_t st) {
   T.mlo.assign(p + 1, nullptr);
   T.map_mhi.resize(p + 1);
   T.map_mlo.resize(p + 1);
-  T.map_ohi.resize(p + 1);
-  T.map_olo.resize(p + 1);
   T.op_exp.assign(p + 1, 0);
   T.maxabs = plan.alloc<float>(p + 1);
   T.mom_exp = plan.alloc<int>(p + 1);
@@ -1027,31 +1199,16 @@ void build_tc(Plan &plan, cudaStream_t st) {
     DFDM_CUDA_TRY(cudaMemcpy(d_dir, op_dir.data(), nops * 3 * 8, cudaMemcpyHostToDevice));
     DFDM_CUDA_TRY(cudaMemcpy(d_w, level_w.data(), level_w.size() * 8, cudaMemcpyHostToDevice));
     DFDM_CUDA_TRY(cudaMemcpy(d_sc, level_scale.data(), level_scale.size() * 4, cudaMemcpyHostToDevice));
-    const size_t ocnt = (size_t)nops * KP * KP;
-    T.ohi = plan.alloc<__half>(ocnt);
-    T.olo = plan.alloc<__half>(ocnt);
+    const size_t ocnt = (size_t)nops * KP * KP * 2;
+    T.opk = plan.alloc<__half>(ocnt);
     k_coupling_split<<<dim3(KP, nops), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
-                                                      d_sc, plan.kappa, T.ohi, T.olo);
+                                                      d_sc, plan.kappa, T.opk);
     DFDM_LAUNCH_CHECK();
     DFDM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_level);
     cudaFree(d_dir);
     cudaFree(d_w);
     cudaFree(d_sc);
-    for (auto &L : plan.levels) {
-      if (L.off.empty()) continue;
-      const int no = (int)L.off.size() / 3;
-      const cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)KP, (cuuint64_t)no};
-      const cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)KP * KP * 2};
-      const cuuint32_t box[3] = {(cuuint32_t)kK, (cuuint32_t)(KP / 2), 1};
-      const cuuint32_t es[3] = {1, 1, 1};
-      __half *bh = T.ohi + (size_t)L.op_base * KP * KP;
-      __half *bl = T.olo + (size_t)L.op_base * KP * KP;
-      encode(&T.map_ohi[L.level], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bh, dims, strides, box, es,
-             CU_TENSOR_MAP_SWIZZLE_32B);
-      encode(&T.map_olo[L.level], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bl, dims, strides, box, es,
-             CU_TENSOR_MAP_SWIZZLE_32B);
-    }
   }
   DFDM_CUDA_TRY(cudaStreamSynchronize(st));
 }
@@ -1112,6 +1269,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.op_off = plan.op_off_dev;
       a.op_slot = plan.op_slot_dev;
       a.op_base = L.op_base;
+      a.opk = T.opk + (size_t)L.op_base * KP * KP * 2;
       a.loc = T.loc32[l];
       a.g = L.grid;
       a.n = N;
@@ -1121,11 +1279,12 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.err = plan.err_flag;
       const int gp = L.grid / 2;
       const int tiles = ((gp + kTX - 1) / kTX) * ((gp + kTY - 1) / kTY) * ((gp + kTZ - 1) / kTZ);
+      size_t ops_alpha = 0;
+      for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
+      a.nsplit = m2l_split(tiles * 8, (int)ops_alpha, T.num_sms);
       const int smem = M2lSmem<NP>::kTotal;
-      DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       PhaseScope sc(tm, kPhM2L0 + l, st);
-      k_m2l_tc<NP><<<dim3(tiles, 8), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], T.map_ohi[l],
-                                                              T.map_olo[l], a);
+      k_m2l_tc<NP><<<dim3(tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
       DFDM_COUNT_LAUNCH(plan);
     }
     {
@@ -1155,11 +1314,18 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
     DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));
   }
   PhaseScope sc(tm, kPhNear, st);
-  k_p2p_f32<<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
-                                                  T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end,
-                                                  1 << p, (float)plan.levels[p].w, plan.near_off_dev,
-                                                  (int)(plan.near_off.size() / 3), (float)plan.kappa, x, T.ysorted,
-                                                  y);
+  if (tt.max_leaf_size <= kSmallLeaf) {
+    k_p2p_small<<<(unsigned)((tt.nleaves * 32 + 255) / 256), 256, 0, st>>>(
+        T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, T.sl, ts.n, ts.perm,
+        ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
+        (int)(plan.near_off.size() / 3), (float)plan.kappa, x, T.ysorted, y);
+  } else {
+    k_p2p_f32<<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
+                                                    T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin,
+                                                    ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
+                                                    (int)(plan.near_off.size() / 3), (float)plan.kappa, x,
+                                                    T.ysorted, y);
+  }
   DFDM_COUNT_LAUNCH(plan);
 }
 

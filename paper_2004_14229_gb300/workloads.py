@@ -10,7 +10,15 @@ Recipe (numpy PCG64 via default_rng, FP64 on the host):
     (drawn as an (N, 2) standard-normal array: column 0 real, column 1 imag);
   * sampled rows: distinct indices, seed 4, sorted ascending;
   * the tensor grid of Sect. 4: coordinates (2n - 1) 2^-k - 1, n = 1 .. 2^k,
-    in [-1, 1]^3, 8^k points, x fastest.
+    in [-1, 1]^3, 8^k points, x fastest;
+  * batches of independent problems (batch_problems): problem i draws from
+    default_rng(100 + i), in order, N log-uniform in [N_lo, N_hi] (rounded),
+    kappa log-uniform in [k_lo, k_hi], targets, sources, then nrhs complex
+    vectors (as complex_normal); the distribution cycles uniform in [0,1)^3,
+    Gaussian about (0.5)^3 with sigma 0.15 (redrawn until inside [0,1)^3),
+    and a shell about (0.5)^3 with uniform direction and radius
+    volume-uniform in [0.45, 0.5].  Tree depth: ceil(log8(N / 64)), at least
+    1, the depth at which Alg. 1 with n_max = 64 stops on uniform points.
 """
 import numpy as np
 
@@ -83,3 +91,46 @@ def workload(name):
         w.setdefault("n_max", 0)
     x = complex_normal(w["n"], SEED_X)
     return t, s, x, w
+
+
+SEED_BATCH = 100
+BATCH_KINDS = ("uniform", "gaussian", "shell")
+
+
+def _points(rng, n, kind):
+    if kind == "uniform":
+        return rng.random((n, 3))
+    if kind == "gaussian":
+        out = np.empty((0, 3))
+        while out.shape[0] < n:
+            z = 0.5 + 0.15 * rng.standard_normal((n, 3))
+            z = z[np.all((z >= 0.0) & (z < 1.0), axis=1)]
+            out = np.concatenate([out, z])
+        return out[:n]
+    if kind == "shell":
+        d = rng.standard_normal((n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        a, b = 0.45, 0.5
+        r = (a ** 3 + rng.random(n) * (b ** 3 - a ** 3)) ** (1.0 / 3.0)
+        return 0.5 + r[:, None] * d
+    raise ValueError(kind)
+
+
+def batch_problems(nprob=64, n_range=(1e4, 1e6), kappa_range=(8.0, 256.0), nrhs=16, seed0=SEED_BATCH):
+    """Independent problems: list of dicts (targets, sources, kappa, max_depth,
+    kind, x of shape (nrhs, N) complex128)."""
+    out = []
+    for i in range(int(nprob)):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        kappa = float(np.exp(rng.uniform(np.log(kappa_range[0]), np.log(kappa_range[1]))))
+        kind = BATCH_KINDS[i % 3]
+        t = _points(rng, n, kind)
+        s = _points(rng, n, kind)
+        x = np.empty((int(nrhs), n), dtype=np.complex128)
+        for r in range(int(nrhs)):
+            z = rng.standard_normal((n, 2))
+            x[r] = z[:, 0] + 1j * z[:, 1]
+        depth = max(1, int(np.ceil(np.log(n / 64.0) / np.log(8.0))))
+        out.append(dict(targets=t, sources=s, kappa=kappa, max_depth=depth, kind=kind, x=x))
+    return out

@@ -1,5 +1,8 @@
 """dfdm_apply does no host synchronisation, so a product can be captured in a
-CUDA graph (torch.cuda.CUDAGraph) and replayed; replays equal eager applies."""
+CUDA graph (torch.cuda.CUDAGraph) and replayed; replays equal eager applies
+(to rounding in the tensor-core form, whose coarse M2L levels split every
+operator list over several CTAs that add into the locals atomically, so the
+FP32 summation order differs from run to run)."""
 import numpy as np
 import pytest
 
@@ -36,5 +39,6 @@ def test_apply_captured_in_cuda_graph(precision):
             torch.cuda.synchronize()
             ref = plan.apply(x)
             torch.cuda.synchronize()
-            assert rel_l2(yout.cpu().numpy(), ref.cpu().numpy()) < 1e-13
+            tol = 1e-13 if precision == pkg.FP64 else 1e-6
+            assert rel_l2(yout.cpu().numpy(), ref.cpu().numpy()) < tol
         plan.check()

@@ -71,3 +71,31 @@ def test_plan_without_gpu_fails_cleanly(lib):
     with pytest.raises(pkg.DFDMError) as e:
         pkg.Plan(pts, pts, 1.0, max_depth=2)
     assert e.value.status in (2, 3)
+
+
+def test_batch_invalid_arguments(lib):
+    import ctypes
+    import numpy as np
+    pts = np.random.default_rng(0).random((10, 3))
+    prob = [dict(targets=pts, sources=pts, kappa=1.0)]
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Batch([], order=3)
+    assert e.value.status == 1
+    p = pkg.Params()
+    assert lib.dfdm_params_default(ctypes.byref(p)) == 0
+    p.n_max = 8                                 # batches use uniform trees
+    arr = (pkg.Problem * 1)()
+    arr[0].targets, arr[0].n_t = pts.ctypes.data, 10
+    arr[0].sources, arr[0].n_s = pts.ctypes.data, 10
+    arr[0].kappa, arr[0].max_depth = 1.0, -1
+    out = ctypes.c_void_p(0)
+    assert lib.dfdm_batch_create(1, arr, ctypes.byref(p), 0, None, ctypes.byref(out)) == 1
+    p.n_max = 0
+    assert lib.dfdm_batch_create(1, arr, ctypes.byref(p), 65, None, ctypes.byref(out)) == 1
+    assert lib.dfdm_batch_destroy(None) == 0
+    assert lib.dfdm_batch_apply(None, None, None, 1, None) == 1
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        with pytest.raises(pkg.DFDMError) as e:
+            pkg.Batch(prob, order=3, max_depth=1, root=((0, 0, 0), 1.0))
+        assert e.value.status in (2, 3)

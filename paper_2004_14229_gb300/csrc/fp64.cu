@@ -67,8 +67,8 @@ __global__ void k_coupling_fp64(int order, int n, const int32_t *op_level,
                                 const int32_t *op_off, const double *op_dir,
                                 const double *level_w, double kappa,
                                 double2 *ops) {
-  const int op = blockIdx.y;
-  const int j = blockIdx.x;
+  const int op = blockIdx.x;   // x: up to 2^31 - 1 operators
+  const int j = blockIdx.y;
   const int l = op_level[op];
   const double w = level_w[l];
   const double h = 0.5 * w;
@@ -600,7 +600,7 @@ void build_operators_fp64(Plan &plan, cudaStream_t st) {
     DFDM_CUDA_TRY(cudaMemcpyAsync(d_dir, op_dir.data(), nops * 3 * 8, cudaMemcpyHostToDevice, st));
     DFDM_CUDA_TRY(cudaMemcpyAsync(d_w, level_w.data(), level_w.size() * 8, cudaMemcpyHostToDevice, st));
     plan.coupling = plan.alloc<double2>((size_t)nops * n * n);
-    dim3 grid(n, nops);
+    dim3 grid(nops, n);
     k_coupling_fp64<<<grid, 128, 0, st>>>(o, n, d_level, plan.op_off_dev, d_dir, d_w, plan.kappa, plan.coupling);
     DFDM_LAUNCH_CHECK();
     DFDM_CUDA_TRY(cudaStreamSynchronize(st));

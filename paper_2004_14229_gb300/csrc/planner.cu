@@ -214,6 +214,9 @@ void build_levels(Plan &plan) {
       direction_vector(plan.l_hf, l, c, v);
       L.dir_vec.insert(L.dir_vec.end(), v, v + 3);
     }
+    // the phase kernels put direction slots on the grid's y dimension
+    if (L.slot_dir.size() > 65535)
+      throw Error{DFDM_ERR_UNSUPPORTED, "more than 65535 direction slots on one level"};
     for (size_t i = 0; i < L.op_dir.size(); ++i) L.op_slot.push_back(L.dir_slot[L.op_dir[i]]);
     for (int alpha = 0; alpha < 8; ++alpha) {
       auto &v = L.alpha_ops[alpha];

@@ -93,8 +93,8 @@ __device__ __forceinline__ int64_t op_image_index(int64_t op, int h, int kc, int
 __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t *op_level,
                                  const int32_t *op_off, const double *op_dir, const double *level_w,
                                  const float *level_scale, double kappa, __half *opk) {
-  const int op = blockIdx.y;
-  const int row = blockIdx.x;  // 0 .. 2 NH - 1
+  const int op = blockIdx.x;   // x: up to 2^31 - 1 operators
+  const int row = blockIdx.y;  // 0 .. 2 NH - 1
   const int l = op_level[op];
   const double w = level_w[l], h = 0.5 * w;
   const float sc = level_scale[l];
@@ -1201,7 +1201,7 @@ void build_tc(Plan &plan, cudaStream_t st) {
     DFDM_CUDA_TRY(cudaMemcpy(d_sc, level_scale.data(), level_scale.size() * 4, cudaMemcpyHostToDevice));
     const size_t ocnt = (size_t)nops * KP * KP * 2;
     T.opk = plan.alloc<__half>(ocnt);
-    k_coupling_split<<<dim3(KP, nops), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
+    k_coupling_split<<<dim3(nops, KP), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
                                                       d_sc, plan.kappa, T.opk);
     DFDM_LAUNCH_CHECK();
     DFDM_CUDA_TRY(cudaStreamSynchronize(st));

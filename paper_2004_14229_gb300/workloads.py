@@ -36,6 +36,7 @@ WORKLOADS = {
     "uniform-8k-k16-d4-o4": dict(n=8192, kappa=16.0, depth=4, order=4),
     "uniform-1M-k64-d6-o5": dict(n=1 << 20, kappa=64.0, depth=6, order=5),
     "uniform-4M-k128-d7-o6": dict(n=1 << 22, kappa=128.0, depth=7, order=6),
+    "uniform-256k-k64-d5-o6": dict(n=1 << 18, kappa=64.0, depth=5, order=6),
     "paper-grid-k6": dict(n=8 ** 6, kappa=6.4, depth=10, order=5, grid=6, n_max=512),
     "paper-grid-k7": dict(n=8 ** 7, kappa=12.8, depth=10, order=5, grid=7, n_max=512),
 }
@@ -133,4 +134,37 @@ def batch_problems(nprob=64, n_range=(1e4, 1e6), kappa_range=(8.0, 256.0), nrhs=
             x[r] = z[:, 0] + 1j * z[:, 1]
         depth = max(1, int(np.ceil(np.log(n / 64.0) / np.log(8.0))))
         out.append(dict(targets=t, sources=s, kappa=kappa, max_depth=depth, kind=kind, x=x))
+    return out
+
+
+SEED_SELECTOR = 7
+
+
+def selector_init(seed=SEED_SELECTOR):
+    """Initial parameters of the 4 -> 64 -> 64 -> 64 -> 2 selector network
+    (8770 float32, layout of include/dfdm.h): Glorot-uniform weights, zero
+    biases, drawn layer by layer from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((64, 4), (64, 64), (64, 64), (2, 64)):
+        a = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-a, a, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def selector_problems(count, seed0=200, n_range=(2000, 8000), kappa_range=(2.0, 48.0)):
+    """Small problems on which the method measures its own error for the
+    selector's training data: problem i draws from default_rng(seed0 + i),
+    in order, N log-uniform in n_range, kappa log-uniform in kappa_range,
+    targets, sources (uniform in [0,1)^3), one complex vector; depth 3."""
+    out = []
+    for i in range(int(count)):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        kappa = float(np.exp(rng.uniform(np.log(kappa_range[0]), np.log(kappa_range[1]))))
+        t = rng.random((n, 3))
+        s = rng.random((n, 3))
+        z = rng.standard_normal((n, 2))
+        out.append(dict(targets=t, sources=s, kappa=kappa, max_depth=3, x=z[:, 0] + 1j * z[:, 1]))
     return out

@@ -283,6 +283,59 @@ dfdm_status dfdm_batch_info(dfdm_batch b, int *nstreams, int *stream_of,
 /* Frees the batch, its graph, streams and plans; NULL is allowed. */
 dfdm_status dfdm_batch_destroy(dfdm_batch b);
 
+/* ------------------------------------------------------- parameter selector
+ * A small perceptron that picks a plan's Chebyshev order and high-frequency
+ * level for a requested accuracy.  The paper fixes one order for all levels
+ * (m = 4 in Sect. 4) and l_hf by its rule (Eq. 11); the selector is the
+ * library's own addition, trained on errors the method itself measures
+ * against direct sums.  Network: 4 -> 64 -> 64 -> 64 -> 2, tanh on the
+ * hidden layers, linear output; every parameter enters the products rounded
+ * to FP16, sums in FP32.  Parameters are a flat float vector of
+ * dfdm_selector_param_count() = 8770 entries: W1 (64 x 4, row-major), b1 (64),
+ * W2 (64 x 64), b2, W3 (64 x 64), b3, W4 (2 x 64), b4 (2).  Features of one
+ * level l (4 floats): l / 10, log2(kappa sqrt(3) w_l) / 8,
+ * log2(1 + n / 8^l) / 16, -log10(tol) / 10, with w_l = root_side / 2^l and n
+ * points.  Outputs (2 floats): (order - 2) / 8 and a direction flag (> 0.5:
+ * the level is treated as high-frequency).  Unless stated, pointers are HOST
+ * pointers; the calls run their kernels on `stream` (device scratch is
+ * allocated and freed in stream order) and return after the results are on
+ * the host.  Errors: INVALID_ARG, OOM, CUDA. */
+int dfdm_selector_param_count(void);
+
+/* The 4 features of level `level` (out: 4 floats). */
+dfdm_status dfdm_selector_features(double kappa, double root_side, int level,
+                                   int64_t n_points, double tol, float *out);
+
+/* y (n x 2) = network(theta; x (n x 4)). */
+dfdm_status dfdm_selector_forward(const float *theta, const float *x,
+                                  int64_t n, float *y, void *stream);
+
+/* Loss L = (1/n) sum_i 1/2 |network(x_i) - t_i|^2 (t: n x 2) and its
+ * gradient w.r.t. theta (grad: 8770 floats; the FP16 rounding of the
+ * weights is passed straight through). */
+dfdm_status dfdm_selector_grad(const float *theta, const float *x,
+                               const float *t, int64_t n, float *grad,
+                               float *loss, void *stream);
+
+/* Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) for
+ * `epochs` steps from theta0; theta_out receives the trained parameters and
+ * losses (epochs floats, may be NULL) the loss before each step.  All
+ * computed by the library's GPU kernels; deterministic. */
+dfdm_status dfdm_selector_train(const float *theta0, const float *x,
+                                const float *t, int64_t n, int epochs,
+                                float lr, float *theta_out, float *losses,
+                                void *stream);
+
+/* Fills p->order and p->l_hf for a product with wave number kappa over
+ * n_points points at relative accuracy tol: the network is evaluated on the
+ * features of levels min(2, D) .. D (D = p->max_depth, root side
+ * p->root_side); order = the mean predicted order over those levels,
+ * rounded (a plan has one order; clamped to 2..10), l_hf = the deepest level
+ * flagged high-frequency (-1 if none).
+ * Errors: INVALID_ARG, NUMERIC (a non-finite network output), OOM, CUDA. */
+dfdm_status dfdm_select_params(const float *theta, double kappa, double tol,
+                               int64_t n_points, dfdm_params *p, void *stream);
+
 /* Description of the last error on this thread (never NULL). */
 const char *dfdm_last_error(void);
 

@@ -10,7 +10,7 @@ import os
 
 import numpy as np
 
-__all__ = ["DFDMError", "Plan", "Batch", "Problem", "Params", "load_library", "LIB_PATH", "EXPORTED_SYMBOLS",
+__all__ = ["DFDMError", "Plan", "Batch", "Selector", "Problem", "Params", "load_library", "LIB_PATH", "EXPORTED_SYMBOLS",
            "FP64", "TC_FP16X3"]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdfdm.so")
@@ -28,6 +28,8 @@ EXPORTED_SYMBOLS = [
     "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows", "dfdm_direct_rows_noalloc",
     "dfdm_batch_create", "dfdm_batch_apply", "dfdm_batch_check", "dfdm_batch_plan",
     "dfdm_batch_info", "dfdm_batch_destroy",
+    "dfdm_selector_param_count", "dfdm_selector_features", "dfdm_selector_forward",
+    "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params",
 ]
 
 
@@ -100,6 +102,12 @@ def load_library():
         "dfdm_batch_plan": [vp, i32, ctypes.POINTER(vp)],
         "dfdm_batch_info": [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(i64)],
         "dfdm_batch_destroy": [vp],
+        "dfdm_selector_param_count": [],
+        "dfdm_selector_features": [dbl, dbl, i32, i64, dbl, vp],
+        "dfdm_selector_forward": [vp, vp, i64, vp, vp],
+        "dfdm_selector_grad": [vp, vp, vp, i64, vp, vp, vp],
+        "dfdm_selector_train": [vp, vp, vp, i64, i32, ctypes.c_float, vp, vp, vp],
+        "dfdm_select_params": [vp, dbl, dbl, i64, ctypes.POINTER(Params), vp],
         "dfdm_last_error": [],
         "dfdm_version": [],
     }
@@ -400,3 +408,62 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Selector:
+    """Learned parameter selector (dfdm_selector_*): a 4 -> 64 -> 64 -> 64 -> 2
+    perceptron with FP16 weights, trained and evaluated by the library's GPU
+    kernels.  theta: the 8770 parameters (float32)."""
+
+    N_PARAMS = 8770
+
+    def __init__(self, theta):
+        self._lib = load_library()
+        self.theta = np.ascontiguousarray(theta, dtype=np.float32).reshape(-1)
+        if self.theta.size != self._lib.dfdm_selector_param_count():
+            raise ValueError("theta must hold %d parameters" % self._lib.dfdm_selector_param_count())
+
+    @staticmethod
+    def features(kappa, root_side, level, n_points, tol):
+        out = np.empty(4, dtype=np.float32)
+        _check(load_library().dfdm_selector_features(float(kappa), float(root_side), int(level),
+                                                     int(n_points), float(tol), out.ctypes.data))
+        return out
+
+    def forward(self, x, stream=None):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        y = np.empty((x.shape[0], 2), dtype=np.float32)
+        _check(self._lib.dfdm_selector_forward(self.theta.ctypes.data, x.ctypes.data, x.shape[0],
+                                               y.ctypes.data, _stream_handle(stream)))
+        return y
+
+    def grad(self, x, t, stream=None):
+        """(loss, gradient) of the mean squared error 1/2 |y - t|^2."""
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1, 2)
+        g = np.empty(self.theta.size, dtype=np.float32)
+        loss = np.empty(1, dtype=np.float32)
+        _check(self._lib.dfdm_selector_grad(self.theta.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0],
+                                            g.ctypes.data, loss.ctypes.data, _stream_handle(stream)))
+        return float(loss[0]), g
+
+    @classmethod
+    def train(cls, theta0, x, t, epochs, lr=1e-3, stream=None):
+        """Full-batch Adam on the GPU; returns (Selector, losses before each step)."""
+        lib = load_library()
+        th0 = np.ascontiguousarray(theta0, dtype=np.float32).reshape(-1)
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1, 2)
+        out = np.empty_like(th0)
+        losses = np.empty(max(int(epochs), 1), dtype=np.float32)
+        _check(lib.dfdm_selector_train(th0.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], int(epochs),
+                                       ctypes.c_float(lr), out.ctypes.data, losses.ctypes.data,
+                                       _stream_handle(stream)))
+        return cls(out), losses[:int(epochs)]
+
+    def select(self, kappa, tol, n_points, max_depth, root_side=1.0, stream=None):
+        """(order, l_hf) the network picks for this product (dfdm_select_params)."""
+        p = _params(self._lib, 5, max_depth, 0, 5.0, None, ((0.0, 0.0, 0.0), root_side), FP64, 1)
+        _check(self._lib.dfdm_select_params(self.theta.ctypes.data, float(kappa), float(tol), int(n_points),
+                                            ctypes.byref(p), _stream_handle(stream)))
+        return int(p.order), int(p.l_hf)

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <map>
 #include <set>
+#include <tuple>
 
 #include "dfdm_internal.cuh"
 
@@ -218,9 +219,17 @@ void build_levels(Plan &plan) {
     if (L.slot_dir.size() > 65535)
       throw Error{DFDM_ERR_UNSUPPORTED, "more than 65535 direction slots on one level"};
     for (size_t i = 0; i < L.op_dir.size(); ++i) L.op_slot.push_back(L.dir_slot[L.op_dir[i]]);
+    // ops grouped by direction slot; inside a slot by the parity class of d,
+    // then by d: consecutive offsets d, d + 2 e_x, ... read source blocks
+    // that overlap by three quarters (the M2L reads sources 2 T + alpha - d)
+    auto okey = [&](int o) {
+      const int *d = &L.off[3 * o];
+      const int par = (d[0] & 1) | ((d[1] & 1) << 1) | ((d[2] & 1) << 2);
+      return std::make_tuple(L.op_slot[o], par, d[2], d[1], d[0]);
+    };
     for (int alpha = 0; alpha < 8; ++alpha) {
       auto &v = L.alpha_ops[alpha];
-      std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return L.op_slot[a] < L.op_slot[b]; });
+      std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return okey(a) < okey(b); });
     }
   }
   for (int l = 0; l < p; ++l) {

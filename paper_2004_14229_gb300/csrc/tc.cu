@@ -403,9 +403,10 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
 
 // ------------------------------------------------------------- M2L (TC)
 // One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
-// grid), one level.  The NP stacked outputs are computed in two passes, one
-// per half of NH = NP / 2 rows (first the real parts, then the imaginary
-// parts).  Per K step of 16:
+// grid), one level, one half of the NP stacked outputs (NH = NP / 2 rows: the
+// real parts or the imaginary parts; the two CTAs of a tile are neighbours in
+// the grid, so they read the same moment tiles at about the same time), one
+// chunk of the operator list.  Per K step of 16:
 //   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[half]
 //   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[half]
 // so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 the cross terms
@@ -511,7 +512,8 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   const int g = args.g, gp = g >> 1;
   const int tiles_x = (gp + kTX - 1) / kTX, tiles_y = (gp + kTY - 1) / kTY;
   const int alpha = blockIdx.y;
-  const int tile = blockIdx.x;
+  const int tile = blockIdx.x >> 1;
+  const int h0 = blockIdx.x & 1;   // output half of this CTA (the two halves of a tile are neighbours)
   const int X0 = (tile % tiles_x) * kTX;
   const int Y0 = ((tile / tiles_x) % tiles_y) * kTY;
   const int Z0 = (tile / (tiles_x * tiles_y)) * kTZ;
@@ -557,7 +559,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       ptx::prefetch_tensormap(&map_mlo);
       uint32_t it = 0;
       bool ok = true;
-      for (int h = 0; h < 2 && ok; ++h) {
+      for (int h = h0; h < h0 + 1 && ok; ++h) {
         for (int ii = i0; ii < i1 && ok; ++ii) {
           const int op = args.alpha_ops[ii];
           const int slot = args.op_slot[op];
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       uint32_t it = 0, groups = 0;
       uint32_t units[2] = {0, 0};   // units issued per TMEM region
       bool ok = true;
-      for (int h = 0; h < 2 && ok; ++h) {
+      for (int h = h0; h < h0 + 1 && ok; ++h) {
         int run = 0;
         for (int ii = i0; ii < i1 && ok; ++ii) {
           const int slot = args.op_slot[args.alpha_ops[ii]];
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       uint32_t drains[2] = {0, 0};   // units drained so far, per TMEM region
       bool stop = false;
-      for (int h = 0; h < 2 && !stop; ++h) {
+      for (int h = h0; h < h0 + 1 && !stop; ++h) {
         int run = 0;
         for (int ii = i0; ii < i1 && !stop; ++ii) {
           const int slot = args.op_slot[args.alpha_ops[ii]];
@@ -829,6 +831,71 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
   }
 }
 
+// Leaves of at most kSmallLeaf points (uniform trees: ~2 points a leaf): one
+// warp per leaf, lanes over the n coefficients of one point at a time (each
+// lane a TwoSum over its n / 32 terms), partial sums reduced across the warp
+// in FP64.
+template <int O>
+__device__ __forceinline__ float pick(const float *a, int i) {
+  float v = a[0];
+#pragma unroll
+  for (int j = 1; j < O; ++j) v = (i == j) ? a[j] : v;
+  return v;
+}
+
+template <int O>
+__global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
+                                                   const int32_t *leaf_begin, const int32_t *leaf_end,
+                                                   int64_t nleaves, double w, const double *dir, int nslots,
+                                                   double kappa, const float *loc, int64_t ncell, int KP,
+                                                   float2 *ysorted) {
+  constexpr int N = O * O * O;
+  constexpr int KPL = (N + 31) / 32;
+  const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (leaf >= nleaves) return;
+  const int cell = leaf_cell[leaf];
+  const float inv_h = (float)(2.0 / w);
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  for (int p = b; p < e; ++p) {
+    const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
+    float lx[O], ly[O], lz[O];
+    lagrange1f<O>(y0 * inv_h, lx);
+    lagrange1f<O>(y1 * inv_h, ly);
+    lagrange1f<O>(y2 * inv_h, lz);
+    double tx = 0.0, ty = 0.0;
+    for (int slot = 0; slot < nslots; ++slot) {
+      const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
+      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll
+      for (int j = 0; j < KPL; ++j) {
+        const int k = lane + 32 * j;
+        if (k < N) {
+          const float l = pick<O>(lx, k % O) * pick<O>(ly, (k / O) % O) * pick<O>(lz, k / (O * O));
+          two_sum_acc(sr, __fmul_rn(l, src[k]), cr);
+          two_sum_acc(si, __fmul_rn(l, src[N + k]), ci);
+        }
+      }
+      double re = (double)sr + (double)cr, im = (double)si + (double)ci;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
+      if (c0 == 0.0 && c1 == 0.0 && c2 == 0.0) {
+        tx += re;
+        ty += im;
+      } else {
+        const float2 ph = cexpi_reduced(kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
+        tx += re * ph.x - im * ph.y;
+        ty += re * ph.y + im * ph.x;
+      }
+    }
+    if (lane == 0) ysorted[p] = make_float2((float)tx, (float)ty);
+  }
+}
+
 // ----------------------------------------------------- nearfield (FP32)
 // One block per target leaf.  Each thread owns up to kP2pT targets of the
 // leaf (strided by the block size); the source points of every nearfield
@@ -883,25 +950,31 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
           sv[threadIdx.x] = x[sperm[q]];
         }
         __syncthreads();
+        // every staged source against the thread's kP2pT targets: independent
+        // accumulation chains, one shared-memory read per source
+        float cr[kP2pT], ci[kP2pT];
 #pragma unroll
-        for (int u = 0; u < kP2pT; ++u) {
-          if (!act[u]) continue;
-          float cr = 0.f, ci = 0.f;
-          for (int k = 0; k < cnt; ++k) {
-            const float4 q = sp[k];
+        for (int u = 0; u < kP2pT; ++u) cr[u] = ci[u] = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+          const float4 q = sp[k];
+          const float2 v = sv[k];
+#pragma unroll
+          for (int u = 0; u < kP2pT; ++u) {
             const float d0 = px[u] - q.x, d1 = py[u] - q.y, d2 = pz[u] - q.z;
             const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            if (r2 == 0.f) continue;   // coincident points (zero diagonal)
-            const float ir = rsqrtf(r2);
+            // coincident points (zero diagonal) and idle target slots add 0
+            const float ir = (r2 > 0.f && act[u]) ? rsqrtf(r2) : 0.f;
             float sn, cs;
             sincosf(kappa * (r2 * ir), &sn, &cs);
             const float sc = inv4pi * ir;
-            const float2 v = sv[k];
-            cr = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr);
-            ci = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci);
+            cr[u] = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr[u]);
+            ci[u] = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci[u]);
           }
-          ar[u] += (double)cr;
-          ai[u] += (double)ci;
+        }
+#pragma unroll
+        for (int u = 0; u < kP2pT; ++u) {
+          ar[u] += (double)cr[u];
+          ai[u] += (double)ci[u];
         }
       }
     }
@@ -1028,21 +1101,35 @@ struct TcState {
   float *tl = nullptr, *sl = nullptr;    // leaf-local coordinates
   float2 *ysorted = nullptr;
   int num_sms = 1;
+  size_t l2_bytes = 0;
 };
 
-// CTAs per (tile, alpha) for one M2L level: with one resident CTA per SM a
-// level of `ctas` CTAs runs in ceil(ctas / num_sms) waves, so a level with
-// few tiles (the coarse levels) leaves SMs idle.  Splitting every operator
-// list into s chunks costs one more flush per chunk; take the smallest s whose
-// waves per unit of work are within 2 % of the best, keeping >= 16 ops a chunk.
-static int m2l_split(int ctas, int ops_per_alpha, int num_sms) {
-  auto cost = [&](int s) { return (double)(((int64_t)ctas * s + num_sms - 1) / num_sms) / s; };
-  int smax = std::max(1, std::min(32, ops_per_alpha / 16));
-  double best = cost(1);
-  for (int s = 2; s <= smax; ++s) best = std::min(best, cost(s));
-  for (int s = 1; s <= smax; ++s)
+// CTAs per (tile, alpha) for one M2L level.  Two reasons to split every
+// operator list into s contiguous chunks (chunks add into the locals
+// atomically):
+//  * waves: with one resident CTA per SM a level of `ctas` CTAs runs in
+//    ceil(ctas / num_sms) waves, so a level with few tiles (the coarse
+//    levels) leaves SMs idle; take the smallest s whose waves per unit of
+//    work are within 2 % of the best, keeping >= 16 ops a chunk;
+//  * L2: when a parity has at least num_sms CTAs (units: tiles x 2 output
+//    halves), all resident CTAs work on one (parity, chunk) at a time (grid x
+//    is the fastest index), so a chunk whose operators fit in 40 % of L2 is
+//    read from HBM about once per chunk instead of once per CTA that falls
+//    out of step with the rest.
+static int m2l_split(int units, int ops_per_alpha, int num_sms, size_t op_bytes, size_t l2_bytes) {
+  const int64_t ctas = (int64_t)units * 8;
+  auto cost = [&](int s) { return (double)((ctas * s + num_sms - 1) / num_sms) / s; };
+  int s_min = 1;
+  if (units >= num_sms && op_bytes > 0) {
+    const int c_max = std::max<int>(16, (int)(0.4 * (double)l2_bytes / (double)op_bytes));
+    s_min = std::max(1, (ops_per_alpha + c_max - 1) / c_max);
+  }
+  const int smax = std::max(s_min, std::min(32, ops_per_alpha / 16));
+  double best = cost(s_min);
+  for (int s = s_min + 1; s <= smax; ++s) best = std::min(best, cost(s));
+  for (int s = s_min; s <= smax; ++s)
     if (cost(s) <= best * 1.02) return s;
-  return 1;
+  return s_min;
 }
 
 static TcState &tc_state(Plan &plan) {
@@ -1063,6 +1150,9 @@ void build_tc(Plan &plan, cudaStream_t st) {
     int dev = 0;
     DFDM_CUDA_TRY(cudaGetDevice(&dev));
     DFDM_CUDA_TRY(cudaDeviceGetAttribute(&T.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    int l2 = 0;
+    DFDM_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    T.l2_bytes = (size_t)l2;
   }
   const int KP = round_up(2 * n, 64);  // stacked length: N halves and H-drain groups of 16
   if (KP / 2 > 256) throw Error{DFDM_ERR_UNSUPPORTED, "order too large for one MMA N half"};
@@ -1281,10 +1371,10 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       const int tiles = ((gp + kTX - 1) / kTX) * ((gp + kTY - 1) / kTY) * ((gp + kTZ - 1) / kTZ);
       size_t ops_alpha = 0;
       for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
-      a.nsplit = m2l_split(tiles * 8, (int)ops_alpha, T.num_sms);
+      a.nsplit = m2l_split(2 * tiles, (int)ops_alpha, T.num_sms, (size_t)KP * KP * 4, T.l2_bytes);
       const int smem = M2lSmem<NP>::kTotal;
       PhaseScope sc(tm, kPhM2L0 + l, st);
-      k_m2l_tc<NP><<<dim3(tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
+      k_m2l_tc<NP><<<dim3(2 * tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
       DFDM_COUNT_LAUNCH(plan);
     }
     {
@@ -1302,7 +1392,12 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       }
     }
     PhaseScope sc(tm, kPhL2T, st);
-    if (nsl > 0 && tt.nleaves > 0) {
+    if (nsl > 0 && tt.nleaves > 0 && tt.max_leaf_size <= kSmallLeaf) {
+      k_l2t_small<O><<<nblk(tt.nleaves * 32, 256), 256, 0, st>>>(
+          T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, P.w, plan.dir_vec_dev + plan.dir_vec_off[p],
+          nsl, plan.kappa, T.loc32[p], 1ll << (3 * p), KP, T.ysorted);
+      DFDM_COUNT_LAUNCH(plan);
+    } else if (nsl > 0 && tt.nleaves > 0) {
       k_l2t_f32<O><<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, P.w,
                                                          plan.dir_vec_dev + plan.dir_vec_off[p], nsl, plan.kappa,
                                                          T.loc32[p], 1ll << (3 * p), KP, T.ysorted);

@@ -1,0 +1,76 @@
+"""Learned parameter selector on the GPU: forward pass, gradient and training
+against the FP64 oracle (oracle/selector.py), and what the trained network
+gains over the fixed rule on problems it did not see."""
+import numpy as np
+import pytest
+
+import paper_2004_14229_gb300 as pkg
+from oracle import selector as S
+from paper_2004_14229_gb300.workloads import selector_init, selector_problems
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+    t = np.stack([0.3 * x[:, 0] - 0.2 * x[:, 1] ** 2, np.tanh(x[:, 2] + x[:, 3])], axis=1).astype(np.float32)
+    return x, t
+
+
+def _theta(seed):
+    th = selector_init(seed).astype(np.float64)
+    th += np.random.default_rng(seed + 1).normal(0, 0.05, th.size)
+    return th.astype(np.float32)
+
+
+def test_forward_and_gradient_match_oracle():
+    x, t = _data(300, 1)
+    th = _theta(2)
+    sel = pkg.Selector(th)
+    y = sel.forward(x)
+    yo, _ = S.forward(th.astype(np.float64), x.astype(np.float64))
+    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) < 1e-5
+    loss, g = sel.grad(x, t)
+    lo, go = S.loss_and_grad(th.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lo) / lo < 1e-5
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-4
+    # every layer's block of the gradient, not just the total
+    for a, b in ((0, 320), (320, 4480), (4480, 8640), (8640, 8770)):
+        assert np.linalg.norm(g[a:b] - go[a:b]) / np.linalg.norm(go[a:b]) < 1e-4, (a, b)
+
+
+def test_training_matches_oracle():
+    x, t = _data(200, 3)
+    th0 = _theta(4)
+    sel, losses = pkg.Selector.train(th0, x, t, epochs=40, lr=3e-3)
+    tho, lo = S.adam_train(th0.astype(np.float64), x.astype(np.float64), t.astype(np.float64), 40, 3e-3)
+    assert np.all(np.abs(losses - lo) <= 1e-3 * lo + 1e-7)
+    assert losses[-1] < 0.5 * losses[0]
+    assert np.linalg.norm(sel.theta - tho) / np.linalg.norm(tho) < 1e-3
+    # deterministic: the same call gives the same bits
+    sel2, losses2 = pkg.Selector.train(th0, x, t, epochs=40, lr=3e-3)
+    assert np.array_equal(sel.theta, sel2.theta) and np.array_equal(losses, losses2)
+
+
+def test_trained_selector_beats_fixed_rule_on_unseen_problems():
+    from paper_2004_14229_gb300 import selector_data as D
+    train = D.measure(selector_problems(8, seed0=200))
+    X, T = D.make_samples(train, np.logspace(-1, -8, 15))
+    sel, losses = pkg.Selector.train(selector_init(), X, T, epochs=1500, lr=3e-3)
+    # the labels are per problem, the features per level: the loss levels off
+    assert losses[-1] < 0.15 * losses[0]
+    fixed = {1e-2: 0, 1e-6: 0}
+    chosen = {1e-2: 0, 1e-6: 0}
+    cheaper = 0
+    for p in selector_problems(3, seed0=900):
+        lhf0 = D.default_l_hf(p)
+        for tol in (1e-2, 1e-6):
+            o, lhf = sel.select(p["kappa"], tol, p["targets"].shape[0], p["max_depth"])
+            chosen[tol] += D.evaluate(p, o, lhf) <= tol
+            fixed[tol] += D.evaluate(p, 5, lhf0) <= tol
+            cheaper += (tol == 1e-2) and o < 5
+    # the fixed rule (order 5 everywhere) overshoots 1e-2 and misses 1e-6 on
+    # these problems; the selector meets both with fewer nodes at 1e-2
+    assert chosen[1e-2] == 3 and cheaper == 3, (chosen, cheaper)
+    assert chosen[1e-6] >= 2 and fixed[1e-6] == 0, (chosen, fixed)

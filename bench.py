@@ -115,6 +115,26 @@ def _config(args, w, world):
             "l2": "inputs larger than L2 (coupling operators streamed every step)"}
 
 
+def _traffic(workload_name):
+    """HBM bytes (read + write) of all M2L launches of one product, from the
+    ncu summary under profiles/ for this workload -- None when there is none
+    or when csrc/tc.cu changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "m2l_tc_%s_dram.txt" % workload_name)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(" "):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2004_14229_gb300", "csrc", "tc.cu")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if fields.get("tc.cu sha1") != sha or "dram bytes per product" not in fields:
+        return None
+    return float(fields["dram bytes per product"])
+
+
 def _oracle_rows_per_sec(targets, sources, kappa, x, nrows):
     from oracle.direct import direct_rows, direct_threads
     rows = sample_rows(targets.shape[0], nrows, seed=5)
@@ -246,7 +266,9 @@ def run_ours(args):
         peak = peaks.get("bf16_tflops_sustained", 1700.0) if prec == pkg.TC_FP16X3 else 1.25
         achieved = flops_step / m2l_s / 1e12
         roofline = {"bound": "tensor" if prec == pkg.TC_FP16X3 else "alu", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": _traffic(args.workload) if prec == pkg.TC_FP16X3 else None,
+                    "traffic_unit": "HBM bytes of all M2L launches of one product (ncu)",
                     "kernel": "k_m2l_tc" if prec == pkg.TC_FP16X3 else "k_m2l_fp64",
                     "peak_source": ("%s sustained bf16 (fp16 has the same nominal rate)" % src)
                     if prec == pkg.TC_FP16X3 else "nominal GB300 FP64",

@@ -244,5 +244,15 @@ __device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
   return d;
 }
 
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;     // 8 rows x 64 B
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;              // SWIZZLE_64B
+  return d;
+}
+
 }  // namespace ptx
 }  // namespace dfdm

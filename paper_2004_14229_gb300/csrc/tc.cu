@@ -85,9 +85,9 @@ __device__ __forceinline__ void atomic_max_abs(float *addr, float v) {
 // so one untiled bulk copy moves a whole stage's operator half.
 __device__ __forceinline__ int64_t op_image_index(int64_t op, int h, int kc, int hl, int j, int e, int KSTEPS,
                                                   int NH) {
-  const int chunk = (e >> 3) ^ ((j >> 2) & 1);
+  const int chunk = (e >> 3) ^ ((j >> 1) & 3);
   const int64_t tile = ((op * 2 + h) * KSTEPS + kc) * 2 + hl;
-  return tile * NH * 16 + j * 16 + chunk * 8 + (e & 7);
+  return tile * NH * 32 + j * 32 + chunk * 8 + (e & 7);
 }
 
 __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t *op_level,
@@ -100,7 +100,7 @@ __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t
   const float sc = level_scale[l];
   const bool im_row = row >= NH;
   const int j = im_row ? row - NH : row;
-  const int KSTEPS = KP / 16;
+  const int KSTEPS = KP / 32;
   const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
   const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
   for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
@@ -128,7 +128,7 @@ __global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t
     }
     const __half hi = __float2half_rn(val);
     const __half lo = __float2half_rn(val - __half2float(hi));
-    const int kc = kk >> 4, e = kk & 15, hh = im_row ? 1 : 0;
+    const int kc = kk >> 5, e = kk & 31, hh = im_row ? 1 : 0;
     opk[op_image_index(op, hh, kc, 0, j, e, KSTEPS, NH)] = hi;
     opk[op_image_index(op, hh, kc, 1, j, e, KSTEPS, NH)] = lo;
   }
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(128) k_m2m_f32(const float *cmom, float *pmom,
 }
 
 template <int O>
-__global__ void __launch_bounds__(128) k_l2l_f32(const float *ploc, float *cloc, int gc, const int32_t *pslots,
+__global__ void __launch_bounds__(128) k_l2l_f32(const double *ploc, double *cloc, int gc, const int32_t *pslots,
                                                  const int32_t *pslot_off, const float2 *phase, int nslot_p,
                                                  const float *e1, int KP) {
   constexpr int N = O * O * O;
@@ -346,10 +346,10 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const float *ploc, float *cloc,
   __syncthreads();
   for (int q = pslot_off[cs]; q < pslot_off[cs + 1]; ++q) {
     const int ps = pslots[q];
-    const float *src = ploc + ((int64_t)ps * ncp + cellp) * KP;
+    const double *src = ploc + ((int64_t)ps * ncp + cellp) * KP;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      ur[k] = src[k];
-      ui[k] = src[N + k];
+      ur[k] = (float)src[k];
+      ui[k] = (float)src[N + k];
     }
     __syncthreads();
     tensor_transfer_f<O>(se1, oct, false, ur, ui, tr, ti);
@@ -370,13 +370,13 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const float *ploc, float *cloc,
     }
     __syncthreads();
   }
-  float *dst = cloc + ((int64_t)cs * ncc + cellc) * KP;
+  double *dst = cloc + ((int64_t)cs * ncc + cellc) * KP;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int k = threadIdx.x + 128 * i;
     if (k < N) {
-      dst[k] += ar[i];
-      dst[N + k] += ai[i];
+      dst[k] += (double)ar[i];
+      dst[N + k] += (double)ai[i];
     }
   }
 }
@@ -403,10 +403,9 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
 
 // ------------------------------------------------------------- M2L (TC)
 // One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
-// grid), one level, one half of the NP stacked outputs (NH = NP / 2 rows: the
-// real parts or the imaginary parts; the two CTAs of a tile are neighbours in
-// the grid, so they read the same moment tiles at about the same time), one
-// chunk of the operator list.  Per K step of 16:
+// grid), one level, one chunk of the operator list.  The NP stacked outputs
+// are computed in two passes, one per half of NH = NP / 2 rows (the real
+// parts, then the imaginary parts).  Per K step of 16:
 //   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[half]
 //   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[half]
 // so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 the cross terms
@@ -427,7 +426,7 @@ struct M2lArgs {
   const int32_t *op_slot;     // slot per global op
   const __half *opk;          // operator images of the level (first op = op_base)
   int op_base;                // first global op of the level
-  float *loc;                 // FP32 locals [slot][cell][KP]
+  double *loc;                // locals [slot][cell][KP], FP64 sums of FP32 partial sums
   int g;                      // level grid
   int n;                      // nodes per box
   int KP;                     // padded stacked length (= NP)
@@ -439,7 +438,7 @@ struct M2lArgs {
 
 constexpr int kTM = 64;                   // targets per CTA
 constexpr int kTX = 4, kTY = 4, kTZ = 4;  // parent-grid block of a CTA
-constexpr int kK = 16;                    // K per stage (32-byte rows)
+constexpr int kK = 32;                    // K per stage (64-byte rows, two MMA K steps)
 constexpr int kKsplit = 2;                // K parts (work units) per operator and half
 constexpr int kM2lWarps = 16;             // 8 H warps, 6 X warps, 6 TMA, 7 MMA
 constexpr int kTmaWarp = 6, kMmaWarp = 7;
@@ -512,8 +511,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   const int g = args.g, gp = g >> 1;
   const int tiles_x = (gp + kTX - 1) / kTX, tiles_y = (gp + kTY - 1) / kTY;
   const int alpha = blockIdx.y;
-  const int tile = blockIdx.x >> 1;
-  const int h0 = blockIdx.x & 1;   // output half of this CTA (the two halves of a tile are neighbours)
+  const int tile = blockIdx.x;
   const int X0 = (tile % tiles_x) * kTX;
   const int Y0 = ((tile / tiles_x) % tiles_y) * kTY;
   const int Z0 = (tile / (tiles_x * tiles_y)) * kTZ;
@@ -559,7 +557,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       ptx::prefetch_tensormap(&map_mlo);
       uint32_t it = 0;
       bool ok = true;
-      for (int h = h0; h < h0 + 1 && ok; ++h) {
+      for (int h = 0; h < 2 && ok; ++h) {
         for (int ii = i0; ii < i1 && ok; ++ii) {
           const int op = args.alpha_ops[ii];
           const int slot = args.op_slot[op];
@@ -575,7 +573,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
             ptx::mbar_expect_tx(&full_bar[st], S::kTx);
             ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
             ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
-            ptx::bulk_load(base + S::kOffOhi, args.opk + (((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 * NH * 16,
+            ptx::bulk_load(base + S::kOffOhi, args.opk + (((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 * NH * 32,
                            2 * S::kO, &full_bar[st]);
           }
         }
@@ -592,7 +590,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       uint32_t it = 0, groups = 0;
       uint32_t units[2] = {0, 0};   // units issued per TMEM region
       bool ok = true;
-      for (int h = h0; h < h0 + 1 && ok; ++h) {
+      for (int h = 0; h < 2 && ok; ++h) {
         int run = 0;
         for (int ii = i0; ii < i1 && ok; ++ii) {
           const int slot = args.op_slot[args.alpha_ops[ii]];
@@ -610,11 +608,15 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
               if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
               ptx::tc_fence_after();
               const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
-              const uint64_t a1 = ptx::sdesc_k_sw32(base + S::kOffMhi);   // [M_hi; M_lo]
-              const uint64_t a2 = ptx::sdesc_k_sw32(base);                // [Z; M_hi]
-              const uint32_t init = (units[r] == 0 && ks == 0) ? 0u : 1u;
-              ptx::mma_f16(d, a1, ptx::sdesc_k_sw32(base + S::kOffOhi), idesc, init);
-              ptx::mma_f16(d, a2, ptx::sdesc_k_sw32(base + S::kOffOlo), idesc, 1u);
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                const uint32_t o = 32u * j;
+                const uint64_t a1 = ptx::sdesc_k_sw64(base + S::kOffMhi + o);
+                const uint64_t a2 = ptx::sdesc_k_sw64(base + o);
+                const uint32_t init = (units[r] == 0 && ks == 0 && j == 0) ? 0u : 1u;
+                ptx::mma_f16(d, a1, ptx::sdesc_k_sw64(base + S::kOffOhi + o), idesc, init);
+                ptx::mma_f16(d, a2, ptx::sdesc_k_sw64(base + S::kOffOlo + o), idesc, 1u);
+              }
               ptx::mma_commit(&empty_bar[st]);
             }
             if (!ok) break;
@@ -653,7 +655,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       uint32_t drains[2] = {0, 0};   // units drained so far, per TMEM region
       bool stop = false;
-      for (int h = h0; h < h0 + 1 && !stop; ++h) {
+      for (int h = 0; h < 2 && !stop; ++h) {
         int run = 0;
         for (int ii = i0; ii < i1 && !stop; ++ii) {
           const int slot = args.op_slot[args.alpha_ops[ii]];
@@ -727,7 +729,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
                 const int XX = X0 + jx, YY = Y0 + jy, ZZ = Z0 + jz;
                 const bool ok_r = XX < gp && YY < gp && ZZ < gp;
                 const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
-                float *dst = args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n;
+                double *dst = args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n;
 #pragma unroll
                 for (int j = 0; j < (NH + 31) / 32; ++j) {
                   const int c = lane + 32 * j;
@@ -735,8 +737,9 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
                     const float val = R[c * kRS + rr];
                     R[c * kRS + rr] = 0.f;
                     if (ok_r && c < n) {
-                      if (shared_out) atomicAdd(dst + c, val * inv);
-                      else dst[c] += val * inv;
+                      const double add = (double)val * (double)inv;
+                      if (shared_out) atomicAdd(dst + c, add);
+                      else dst[c] += add;
                     }
                   }
                 }
@@ -774,7 +777,7 @@ __device__ __forceinline__ void two_sum_acc(float &s, float t, float &c) {
 template <int O>
 __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
                                                  const int32_t *leaf_begin, const int32_t *leaf_end, double w,
-                                                 const double *dir, int nslots, double kappa, const float *loc,
+                                                 const double *dir, int nslots, double kappa, const double *loc,
                                                  int64_t ncell, int KP, float2 *ysorted) {
   constexpr int N = O * O * O;
   __shared__ float g[2 * N];
@@ -797,9 +800,9 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
     lagrange1f<O>(y2 * inv_h, lz);
     double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
-      const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
+      const double *src = loc + ((int64_t)slot * ncell + cell) * KP;
       __syncthreads();
-      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = src[i];
+      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = (float)src[i];
       __syncthreads();
       float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
 #pragma unroll
@@ -847,7 +850,7 @@ template <int O>
 __global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
                                                    const int32_t *leaf_begin, const int32_t *leaf_end,
                                                    int64_t nleaves, double w, const double *dir, int nslots,
-                                                   double kappa, const float *loc, int64_t ncell, int KP,
+                                                   double kappa, const double *loc, int64_t ncell, int KP,
                                                    float2 *ysorted) {
   constexpr int N = O * O * O;
   constexpr int KPL = (N + 31) / 32;
@@ -865,15 +868,15 @@ __global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_
     lagrange1f<O>(y2 * inv_h, lz);
     double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
-      const float *src = loc + ((int64_t)slot * ncell + cell) * KP;
+      const double *src = loc + ((int64_t)slot * ncell + cell) * KP;
       float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
 #pragma unroll
       for (int j = 0; j < KPL; ++j) {
         const int k = lane + 32 * j;
         if (k < N) {
           const float l = pick<O>(lx, k % O) * pick<O>(ly, (k / O) % O) * pick<O>(lz, k / (O * O));
-          two_sum_acc(sr, __fmul_rn(l, src[k]), cr);
-          two_sum_acc(si, __fmul_rn(l, src[N + k]), ci);
+          two_sum_acc(sr, __fmul_rn(l, (float)src[k]), cr);
+          two_sum_acc(si, __fmul_rn(l, (float)src[N + k]), ci);
         }
       }
       double re = (double)sr + (double)cr, im = (double)si + (double)ci;
@@ -1089,7 +1092,8 @@ void encode(CUtensorMap *m, CUtensorMapDataType dt, int rank, void *ptr, const c
 // Per-plan state of the tensor-core form.
 struct TcState {
   int KP = 0;                            // = NP, padded stacked length
-  std::vector<float *> mom32, loc32;     // per level FP32 grids
+  std::vector<float *> mom32;            // per level FP32 moment grids
+  std::vector<double *> loc64;           // per level local grids (FP64 sums)
   std::vector<__half *> mhi, mlo;        // per level split moments
   std::vector<CUtensorMap> map_mhi, map_mlo;
   __half *opk = nullptr;                 // split operator images (see op_image_index)
@@ -1111,9 +1115,9 @@ struct TcState {
 //    ceil(ctas / num_sms) waves, so a level with few tiles (the coarse
 //    levels) leaves SMs idle; take the smallest s whose waves per unit of
 //    work are within 2 % of the best, keeping >= 16 ops a chunk;
-//  * L2: when a parity has at least num_sms CTAs (units: tiles x 2 output
-//    halves), all resident CTAs work on one (parity, chunk) at a time (grid x
-//    is the fastest index), so a chunk whose operators fit in 40 % of L2 is
+//  * L2: when a parity has at least num_sms CTAs (units: tiles), all
+//    resident CTAs work on one (parity, chunk) at a time (grid x is the
+//    fastest index), so a chunk whose operators fit in 40 % of L2 is
 //    read from HBM about once per chunk instead of once per CTA that falls
 //    out of step with the rest.
 static int m2l_split(int units, int ops_per_alpha, int num_sms, size_t op_bytes, size_t l2_bytes) {
@@ -1229,7 +1233,7 @@ void build_tc(Plan &plan, cudaStream_t st) {
   T.ysorted = plan.alloc<float2>(plan.tt.n);
   // grids
   T.mom32.assign(p + 1, nullptr);
-  T.loc32.assign(p + 1, nullptr);
+  T.loc64.assign(p + 1, nullptr);
   T.mhi.assign(p + 1, nullptr);
   T.mlo.assign(p + 1, nullptr);
   T.map_mhi.resize(p + 1);
@@ -1241,7 +1245,7 @@ void build_tc(Plan &plan, cudaStream_t st) {
   for (int l = plan.min_level; l <= p; ++l) {
     const size_t cnt = plan.levels[l].slot_dir.size() * ((size_t)1 << (3 * l)) * KP;
     T.mom32[l] = plan.alloc<float>(cnt);
-    T.loc32[l] = plan.alloc<float>(cnt);
+    T.loc64[l] = plan.alloc<double>(cnt);
     if (!plan.levels[l].off.empty()) {
       T.mhi[l] = plan.alloc<__half>(cnt);
       T.mlo[l] = plan.alloc<__half>(cnt);
@@ -1253,9 +1257,9 @@ void build_tc(Plan &plan, cudaStream_t st) {
       const cuuint32_t box[5] = {(cuuint32_t)kK, 2 * kTX, 2 * kTY, 2 * kTZ, 1};
       const cuuint32_t es[5] = {1, 2, 2, 2, 1};
       encode(&T.map_mhi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mhi[l], dims, strides, box, es,
-             CU_TENSOR_MAP_SWIZZLE_32B);
+             CU_TENSOR_MAP_SWIZZLE_64B);
       encode(&T.map_mlo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mlo[l], dims, strides, box, es,
-             CU_TENSOR_MAP_SWIZZLE_32B);
+             CU_TENSOR_MAP_SWIZZLE_64B);
     }
   }
   // split operators, one scale per level: |A~| <= 1 / (4 pi w (2 - r_max))
@@ -1318,8 +1322,8 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       PhaseScope sc(tm, kPhS2M, st);
       DFDM_CUDA_TRY(cudaMemsetAsync(T.maxabs, 0, (p + 1) * sizeof(float), st));
       for (int l = plan.min_level; l <= p; ++l) {
-        const size_t bytes = plan.levels[l].slot_dir.size() * ((size_t)1 << (3 * l)) * KP * sizeof(float);
-        DFDM_CUDA_TRY(cudaMemsetAsync(T.loc32[l], 0, bytes, st));
+        const size_t bytes = plan.levels[l].slot_dir.size() * ((size_t)1 << (3 * l)) * KP * sizeof(double);
+        DFDM_CUDA_TRY(cudaMemsetAsync(T.loc64[l], 0, bytes, st));
       }
       const size_t bytes = P.slot_dir.size() * ((size_t)1 << (3 * p)) * KP * sizeof(float);
       DFDM_CUDA_TRY(cudaMemsetAsync(T.mom32[p], 0, bytes, st));
@@ -1360,7 +1364,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.op_slot = plan.op_slot_dev;
       a.op_base = L.op_base;
       a.opk = T.opk + (size_t)L.op_base * KP * KP * 2;
-      a.loc = T.loc32[l];
+      a.loc = T.loc64[l];
       a.g = L.grid;
       a.n = N;
       a.KP = KP;
@@ -1371,10 +1375,10 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       const int tiles = ((gp + kTX - 1) / kTX) * ((gp + kTY - 1) / kTY) * ((gp + kTZ - 1) / kTZ);
       size_t ops_alpha = 0;
       for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
-      a.nsplit = m2l_split(2 * tiles, (int)ops_alpha, T.num_sms, (size_t)KP * KP * 4, T.l2_bytes);
+      a.nsplit = m2l_split(tiles, (int)ops_alpha, T.num_sms, (size_t)KP * KP * 4, T.l2_bytes);
       const int smem = M2lSmem<NP>::kTotal;
       PhaseScope sc(tm, kPhM2L0 + l, st);
-      k_m2l_tc<NP><<<dim3(2 * tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
+      k_m2l_tc<NP><<<dim3(tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
       DFDM_COUNT_LAUNCH(plan);
     }
     {
@@ -1386,7 +1390,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
         if (nsp == 0 || nsc == 0) continue;
         const float2 *ph = plan.m2m_phase_off[l] >= 0 ? T.phase + plan.m2m_phase_off[l] : nullptr;
         k_l2l_f32<O><<<dim3((unsigned)(1ll << (3 * (l + 1))), nsc), 128, 0, st>>>(
-            T.loc32[l], T.loc32[l + 1], C.grid, plan.l2l_pslots_dev + plan.l2l_pslots_off[l],
+            T.loc64[l], T.loc64[l + 1], C.grid, plan.l2l_pslots_dev + plan.l2l_pslots_off[l],
             plan.l2l_poff_dev + plan.l2l_poff_off[l], ph, nsp, T.e1, KP);
         DFDM_COUNT_LAUNCH(plan);
       }
@@ -1395,12 +1399,12 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
     if (nsl > 0 && tt.nleaves > 0 && tt.max_leaf_size <= kSmallLeaf) {
       k_l2t_small<O><<<nblk(tt.nleaves * 32, 256), 256, 0, st>>>(
           T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, P.w, plan.dir_vec_dev + plan.dir_vec_off[p],
-          nsl, plan.kappa, T.loc32[p], 1ll << (3 * p), KP, T.ysorted);
+          nsl, plan.kappa, T.loc64[p], 1ll << (3 * p), KP, T.ysorted);
       DFDM_COUNT_LAUNCH(plan);
     } else if (nsl > 0 && tt.nleaves > 0) {
       k_l2t_f32<O><<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, P.w,
                                                          plan.dir_vec_dev + plan.dir_vec_off[p], nsl, plan.kappa,
-                                                         T.loc32[p], 1ll << (3 * p), KP, T.ysorted);
+                                                         T.loc64[p], 1ll << (3 * p), KP, T.ysorted);
       DFDM_COUNT_LAUNCH(plan);
     } else {
       DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));

@@ -7,10 +7,11 @@ Eq. (1) summed directly on the GPU (dfdm_direct_rows): the relative l2 error
 on sampled rows.  Orders up to 5 use the tensor-core form (their errors, above
 1e-5, are far above its ~1e-6 rounding), orders 6 and 7 the FP64 form.  For a
 tolerance tol, the label of every level l of the problem is
-  * order: the smallest measured order whose error (default l_hf) is <= tol
-    (8 when none is), scaled to (order - 2) / 8;
+  * order: the smallest measured order whose error (default l_hf) is <= tol / 3
+    (a safety factor, so that the network's picks meet tol; 8 when none is),
+    scaled to (order - 2) / 8;
   * direction flag: 1 when l <= l_hf_needed, where l_hf_needed = l_hf - 1 if
-    that coarser choice still meets tol at the chosen order, else l_hf;
+    that coarser choice still meets tol / 3 at the chosen order, else l_hf;
 and its features are dfdm_selector_features(kappa, root side, l, N, tol).
 """
 import numpy as np
@@ -77,13 +78,17 @@ def measure(problems, orders=ORDERS, nrows=64, seed=13):
     return recs
 
 
-def labels(rec, tol, orders=ORDERS):
+SAFETY = 3.0   # labels ask for an error of tol / SAFETY: the network's picks then meet tol
+
+
+def labels(rec, tol, orders=ORDERS, safety=SAFETY):
     """(order needed, l_hf needed) of one record at tolerance tol."""
-    ok = [o for o in orders if rec["err"][(o, 0)] <= tol]
+    goal = tol / safety
+    ok = [o for o in orders if rec["err"][(o, 0)] <= goal]
     o_need = min(ok) if ok else orders[-1] + 1
     lhf_need = rec["l_hf"]
     o_chk = min(o_need, orders[-1])
-    if (o_chk, -1) in rec["err"] and rec["err"][(o_chk, -1)] <= tol:
+    if (o_chk, -1) in rec["err"] and rec["err"][(o_chk, -1)] <= goal:
         lhf_need = rec["l_hf"] - 1
     return o_need, lhf_need
 

@@ -60,17 +60,17 @@ def test_trained_selector_beats_fixed_rule_on_unseen_problems():
     sel, losses = pkg.Selector.train(selector_init(), X, T, epochs=1500, lr=3e-3)
     # the labels are per problem, the features per level: the loss levels off
     assert losses[-1] < 0.15 * losses[0]
-    fixed = {1e-2: 0, 1e-6: 0}
-    chosen = {1e-2: 0, 1e-6: 0}
+    fixed = {1e-2: 0, 1e-5: 0}
+    chosen = {1e-2: 0, 1e-5: 0}
     cheaper = 0
     for p in selector_problems(3, seed0=900):
         lhf0 = D.default_l_hf(p)
-        for tol in (1e-2, 1e-6):
+        for tol in (1e-2, 1e-5):
             o, lhf = sel.select(p["kappa"], tol, p["targets"].shape[0], p["max_depth"])
             chosen[tol] += D.evaluate(p, o, lhf) <= tol
             fixed[tol] += D.evaluate(p, 5, lhf0) <= tol
             cheaper += (tol == 1e-2) and o < 5
-    # the fixed rule (order 5 everywhere) overshoots 1e-2 and misses 1e-6 on
-    # these problems; the selector meets both with fewer nodes at 1e-2
+    # the fixed rule (order 5 everywhere) overshoots 1e-2 and misses 1e-5 on
+    # these problems; the selector meets both, with fewer nodes at 1e-2
     assert chosen[1e-2] == 3 and cheaper == 3, (chosen, cheaper)
-    assert chosen[1e-6] >= 2 and fixed[1e-6] == 0, (chosen, fixed)
+    assert chosen[1e-5] >= 2 and fixed[1e-5] == 0, (chosen, fixed)

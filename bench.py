@@ -115,6 +115,22 @@ def _config(args, w, world):
             "l2": "inputs larger than L2 (coupling operators streamed every step)"}
 
 
+def max_over_ranks(seconds, world, device="cuda"):
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if world <= 1:
+        return float(seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed / the slowest time."""
+    return world * units_per_rank / seconds
+
+
 def _traffic(workload_name):
     """HBM bytes (read + write) of all M2L launches of one product, from the
     ncu summary under profiles/ for this workload -- None when there is none
@@ -229,12 +245,8 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     plan.set_timing(False)
     plan.check()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+    value = job_rate(args.steps, world, elapsed)
 
     # accuracy against the FP64 oracle on stored rows (written by the oracle)
     err = None
@@ -366,13 +378,9 @@ def run_batch(args):
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     batch.check()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
     units = len(probs) * nrhs
-    value = world * units * args.steps / elapsed
+    value = job_rate(units * args.steps, world, elapsed)
     _, _, launches = batch.info()
 
     # error of three problems against exact direct-sum rows (approximation error)

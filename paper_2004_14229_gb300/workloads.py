@@ -156,13 +156,15 @@ def selector_init(seed=SEED_SELECTOR):
 def selector_problems(count, seed0=200, n_range=(2000, 8000), kappa_range=(2.0, 48.0)):
     """Small problems on which the method measures its own error for the
     selector's training data: problem i draws from default_rng(seed0 + i),
-    in order, N log-uniform in n_range, kappa log-uniform in kappa_range,
-    targets, sources (uniform in [0,1)^3), one complex vector; depth 3."""
+    in order, N log-uniform in n_range, kappa log-uniform in the i-th of
+    `count` equal log-intervals of kappa_range (so the problems cover the
+    range), targets, sources (uniform in [0,1)^3), one complex vector; depth 3."""
     out = []
+    lk0, lk1 = np.log(kappa_range[0]), np.log(kappa_range[1])
     for i in range(int(count)):
         rng = np.random.default_rng(seed0 + i)
         n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
-        kappa = float(np.exp(rng.uniform(np.log(kappa_range[0]), np.log(kappa_range[1]))))
+        kappa = float(np.exp(lk0 + (i + rng.uniform()) * (lk1 - lk0) / count))
         t = rng.random((n, 3))
         s = rng.random((n, 3))
         z = rng.standard_normal((n, 2))

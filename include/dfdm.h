@@ -49,8 +49,9 @@ typedef enum {
   DFDM_FP64 = 0,
   /* Coupling (M2L) products on the tcgen05 tensor cores with operands split
    * into two FP16 terms (hi + lo, three products hi*hi + hi*lo + lo*hi) and
-   * FP32 accumulation; the other phases in FP32 with FP64 argument
-   * reduction of kappa |x - y| and of the plane-wave phases. */
+   * FP32 accumulation, local expansions summed in FP64; the other phases in
+   * FP32 with FP64 argument reduction of kappa |x - y| and of the
+   * plane-wave phases.  Orders 2..6. */
   DFDM_TC_FP16X3 = 1
 } dfdm_precision;
 
@@ -103,7 +104,8 @@ dfdm_status dfdm_params_default(dfdm_params *p);
  * kappa > 0.  Errors: INVALID_ARG for kappa <= 0 or not finite, n < 1,
  * non-finite coordinates, points outside the root cube (root_mode 0),
  * order outside 2..10, max_depth outside 0..10, eta2 <= 0;
- * UNSUPPORTED when the two trees are not both of uniform depth (all leaves
+ * UNSUPPORTED for the tensor-core form at orders above 6, and when the two
+ * trees are not both of uniform depth (all leaves
  * on one level p; always true for n_max = 0); OOM; CUDA.
  * On success *out receives the plan; on failure *out is NULL.  The work is
  * done on `stream`; the call returns after it finished. */

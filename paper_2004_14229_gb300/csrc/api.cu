@@ -129,6 +129,8 @@ dfdm_status dfdm_plan_create(const double *targets, int64_t n_t,
   if (pr.nrhs_max < 1) return fail(DFDM_ERR_INVALID_ARG, "nrhs_max must be >= 1");
   if (pr.precision != DFDM_FP64 && pr.precision != DFDM_TC_FP16X3)
     return fail(DFDM_ERR_INVALID_ARG, "unknown precision");
+  if (pr.precision == DFDM_TC_FP16X3 && pr.order > 6)
+    return fail(DFDM_ERR_UNSUPPORTED, "the tensor-core form supports orders 2..6");
   if (pr.root_mode != 0 && pr.root_mode != 1) return fail(DFDM_ERR_INVALID_ARG, "root_mode must be 0 or 1");
   if (!finite_points(targets, n_t) || !finite_points(sources, n_s))
     return fail(DFDM_ERR_INVALID_ARG, "coordinates must be finite");

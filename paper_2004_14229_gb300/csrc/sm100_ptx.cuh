@@ -1,6 +1,7 @@
 // Inline-PTX building blocks for Blackwell (sm_100 family, here sm_103a):
-// mbarriers with bounded waits, TMA tile loads, TMEM allocation, tcgen05 MMA
-// (kind::f16, FP32 accumulator in TMEM), commit and TMEM loads.
+// mbarriers with bounded waits, TMA tile and untiled bulk loads, TMEM
+// allocation, tcgen05 MMA (kind::f16, FP32 accumulator in TMEM), commit,
+// TMEM loads and stores, named barriers.
 //
 // Every wait in this file has an iteration limit.  A wait that gives up
 // returns false; callers record an error word and leave the kernel instead
@@ -60,23 +61,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   return false;
 }
 
-// ------------------------------------------------------------------ TMA
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
-                                            int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                            int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
                                             int c2, int c3, int c4) {
   asm volatile(
@@ -85,8 +69,6 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
       "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
       : "memory");
 }
-// Multicast variant: the tile lands at the same CTA-relative offset in every
-// CTA of `mask` in the cluster and signals each one's mbarrier at `bar`'s offset.
 // Untiled bulk copy global -> this CTA's shared memory, completion counted
 // on `bar` in bytes.  dst and src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -94,27 +76,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                               int c2, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
-      "[%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
@@ -140,19 +101,6 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// ------------------------------------------------------------------ MMA
-// Shared-memory matrix descriptor of a K-major operand tile stored with the
-// 128-byte swizzle: rows of 64 FP16 (128 B), 8-row atoms of 1024 B.
-__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address
-  d |= (uint64_t)1u << 16;                         // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1u << 46;                         // descriptor version (sm_100)
-  d |= (uint64_t)2u << 61;                         // SWIZZLE_128B
-  return d;
-}
-
 // Instruction descriptor, kind::f16: FP16 A and B (K-major), FP32 D.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int m, int n) {
   return (1u << 4)                       // D: F32
@@ -176,16 +124,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
-}
-
-// Arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once the
-// MMAs issued so far by this thread have completed.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 // 32 lanes x 32 bit, 16 consecutive columns per thread.
@@ -232,18 +170,9 @@ __device__ __forceinline__ bool named_bar_or(int id, int count, bool v) {
   return r != 0;
 }
 
-// Shared-memory matrix descriptor of a K-major operand tile stored with the
-// 32-byte swizzle: rows of 16 FP16 (32 B), 8-row atoms of 256 B.
-__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(256u >> 4) << 32;     // 8 rows x 32 B
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)6u << 61;              // SWIZZLE_32B
-  return d;
-}
-
+// Shared-memory matrix descriptor of a K-major operand tile in the 64-byte
+// swizzle: rows of 64 B (32 FP16 of K), 8-row atoms of 512 B (stride byte
+// offset), start address advanced by 32 B for the second K step of 16.
 __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);

@@ -502,8 +502,8 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
   static_assert(KSTEPS % kKsplit == 0, "K steps must split evenly");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NH][kTM]
-  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full[2], acc_empty[2], grp_done;
+  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NH][kRS]
+  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full[2], acc_empty[2], grp_done, mma_fin;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
       ptx::mbar_init(&acc_empty[r], 8);
     }
     ptx::mbar_init(&grp_done, kEpiWarps);
+    ptx::mbar_init(&mma_fin, 1);
     s_abort = 0;
     ptx::fence_mbar_init();
   }
@@ -578,6 +579,10 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
           }
         }
       }
+      // copies still in flight land before the CTA leaves: wait (bounded) for
+      // the last phase of every stage filled (already complete on a normal run)
+      for (uint32_t k = (it > (uint32_t)kSt ? it - kSt : 0u); k < it; ++k)
+        if (!ptx::mbar_wait(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
       if (!ok) {
         atomicExch(args.err, 1);
         atomicExch(&s_abort, 1);
@@ -634,6 +639,10 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
           }
         }
       }
+      // every MMA issued has finished reading shared memory and writing TMEM
+      // before the CTA frees them (bounded; immediate on a normal run)
+      ptx::mma_commit(&mma_fin);
+      if (!ptx::mbar_wait(&mma_fin, 0, kWaitLimit)) ok = false;
       if (!ok) {
         atomicExch(args.err, 1);
         atomicExch(&s_abort, 1);
@@ -943,8 +952,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
       const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
       if (s < 0) continue;
       const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
-      for (int q0 = sb[s]; q0 < se[s]; q0 += 128) {
-        const int cnt = min(128, se[s] - q0);
+      for (int q0 = sb[s]; q0 < se[s]; q0 += blockDim.x) {   // chunks of one source per thread
+        const int cnt = min((int)blockDim.x, se[s] - q0);
         __syncthreads();
         if (threadIdx.x < cnt) {
           const int q = q0 + threadIdx.x;
@@ -1419,7 +1428,10 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
         ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
         (int)(plan.near_off.size() / 3), (float)plan.kappa, x, T.ysorted, y);
   } else {
-    k_p2p_f32<<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
+    // one block per target leaf; leaves of a few dozen points (uniform trees
+    // just above the warp-per-leaf size) get one warp, large ones 4 warps
+    const unsigned p2p_threads = (tt.n <= 64 * tt.nleaves) ? 32u : 128u;
+    k_p2p_f32<<<(unsigned)tt.nleaves, p2p_threads, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
                                                     T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin,
                                                     ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
                                                     (int)(plan.near_off.size() / 3), (float)plan.kappa, x,

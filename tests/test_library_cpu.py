@@ -58,6 +58,9 @@ def test_invalid_arguments_return_status(lib):
     with pytest.raises(pkg.DFDMError) as e:
         pkg.Plan(pts + 2.0, pts, 1.0)          # outside the unit root cube
     assert e.value.status == 1
+    with pytest.raises(pkg.DFDMError) as e:
+        pkg.Plan(pts, pts, 1.0, order=7, precision=pkg.TC_FP16X3)   # tensor-core form: orders 2..6
+    assert e.value.status == 6
     assert lib.dfdm_plan_destroy(None) == 0
     assert lib.dfdm_apply(None, None, None, 1, None) == 1
 

@@ -41,7 +41,7 @@ typedef enum {
   DFDM_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
   DFDM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up          */
   DFDM_ERR_NUMERIC = 5,     /* a scale or value left its representable range */
-  DFDM_ERR_UNSUPPORTED = 6  /* valid input this build does not handle yet  */
+  DFDM_ERR_UNSUPPORTED = 6  /* valid input the library does not handle yet */
 } dfdm_status;
 
 typedef enum {

@@ -19,7 +19,7 @@ Matrix-Vector Multiplication".  The code follows the paper's order:
   Sect. 2.7                8 reference E_{t'}, one A per    mode="reuse"
                            reference configuration
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
   R1  Eq. (4) prints cos((2 nu - 1)/(2 pi (m+1))); the misplaced pi is read as
       cos((2 nu - 1) pi / (2 (m+1))), the Chebyshev points of the first kind.
   R2  "order" o = m + 1 nodes per axis; multi-index k = nu_x + o nu_y + o^2 nu_z.

@@ -102,3 +102,32 @@ def test_batch_invalid_arguments(lib):
         with pytest.raises(pkg.DFDMError) as e:
             pkg.Batch(prob, order=3, max_depth=1, root=((0, 0, 0), 1.0))
         assert e.value.status in (2, 3)
+
+
+def test_selector_features_and_argument_checks(lib):
+    import ctypes
+    import numpy as np
+    assert lib.dfdm_selector_param_count() == 8770
+    # the four features of include/dfdm.h, written out
+    kappa, side, level, n, tol = 40.0, 2.0, 3, 100000, 1e-5
+    f = pkg.Selector.features(kappa, side, level, n, tol)
+    w = side / 2 ** level
+    want = [level / 10, np.log2(kappa * np.sqrt(3) * w) / 8, np.log2(1 + n / 8 ** level) / 16, 5 / 10]
+    assert np.allclose(f, want, rtol=1e-6)
+    out = np.empty(4, dtype=np.float32)
+    for bad in ((0.0, 1.0, 2, 10, 1e-3), (1.0, -1.0, 2, 10, 1e-3), (1.0, 1.0, -1, 10, 1e-3),
+                (1.0, 1.0, 2, 0, 1e-3), (1.0, 1.0, 2, 10, 0.0)):
+        assert lib.dfdm_selector_features(*bad, out.ctypes.data) == 1
+    th = np.zeros(8770, dtype=np.float32)
+    x = np.zeros(4, dtype=np.float32)
+    y = np.zeros(2, dtype=np.float32)
+    assert lib.dfdm_selector_forward(None, x.ctypes.data, 1, y.ctypes.data, None) == 1
+    assert lib.dfdm_selector_forward(th.ctypes.data, x.ctypes.data, 0, y.ctypes.data, None) == 1
+    assert lib.dfdm_selector_train(th.ctypes.data, x.ctypes.data, y.ctypes.data, 1, 5, ctypes.c_float(0.0),
+                                   th.ctypes.data, None, None) == 1
+    p = pkg.Params()
+    assert lib.dfdm_params_default(ctypes.byref(p)) == 0
+    p.max_depth = 11
+    assert lib.dfdm_select_params(th.ctypes.data, 10.0, 1e-4, 1000, ctypes.byref(p), None) == 1
+    with pytest.raises(ValueError):
+        pkg.Selector(np.zeros(10, dtype=np.float32))

@@ -71,6 +71,13 @@ __device__ __forceinline__ float2 cexpi_reduced(double a) {
   return make_float2(c, s);
 }
 
+// |v| with every non-finite value mapped to +inf (fmaxf would drop a NaN),
+// so a level maximum shows that the level holds a non-finite moment
+__device__ __forceinline__ float abs_or_inf(float v) {
+  const float a = fabsf(v);
+  return (a <= 3.402823466e38f) ? a : __int_as_float(0x7f800000);
+}
+
 __device__ __forceinline__ void atomic_max_abs(float *addr, float v) {
   atomicMax(reinterpret_cast<int *>(addr), __float_as_int(fabsf(v)));
 }
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(128) k_s2m_f32(const float *lxyz, int64_t n_pt
     if (k < N) {
       dst[k] = acc[i].x;
       dst[N + k] = acc[i].y;
-      mx = fmaxf(mx, fmaxf(fabsf(acc[i].x), fabsf(acc[i].y)));
+      mx = fmaxf(mx, fmaxf(abs_or_inf(acc[i].x), abs_or_inf(acc[i].y)));
     }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(128) k_m2m_f32(const float *cmom, float *pmom,
     if (k < N) {
       dst[k] = ar[i];
       dst[N + k] = ai[i];
-      mx = fmaxf(mx, fmaxf(fabsf(ar[i]), fabsf(ai[i])));
+      mx = fmaxf(mx, fmaxf(abs_or_inf(ar[i]), abs_or_inf(ai[i])));
     }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -383,14 +390,26 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const double *ploc, double *clo
 
 // ------------------------------------------------ FP32 -> FP16 hi/lo split
 __global__ void k_split(const float *src, int64_t count, const float *maxabs, int *exp_out, __half *hi,
-                        __half *lo) {
-  // scale 2^e with max * 2^e <= 2^14
+                        __half *lo, int *err) {
+  // scale 2^e with max * 2^e <= 2^14; a level maximum that is not finite, or
+  // that the clamped scale cannot bring into FP16's normal range, is a
+  // numeric error (error word 2, kept if an earlier error is already there)
   const float mx = *maxabs;
   int e = 0;
-  if (mx > 0.f) e = 14 - (int)ceilf(log2f(mx));
-  if (e > 60) e = 60;
-  if (e < -60) e = -60;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = e;
+  bool bad = !(mx >= 0.f) || isinf(mx);
+  if (!bad && mx > 0.f) e = 14 - (int)ceilf(log2f(mx));
+  if (e > 60) {
+    e = 60;
+    bad = bad || ldexpf(mx, e) < 0x1p-14f;
+  }
+  if (e < -60) {
+    e = -60;
+    bad = bad || ldexpf(mx, e) > 65504.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *exp_out = e;
+    if (bad) atomicCAS(err, 0, 2);
+  }
   const float sc = ldexpf(1.0f, e);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1363,7 +1382,8 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       {
         PhaseScope sc(tm, kPhSplit, st);
         const int64_t cnt = (int64_t)L.slot_dir.size() * (1ll << (3 * l)) * KP;
-        k_split<<<1184, 256, 0, st>>>(T.mom32[l], cnt, T.maxabs + l, T.mom_exp + l, T.mhi[l], T.mlo[l]);
+        k_split<<<1184, 256, 0, st>>>(T.mom32[l], cnt, T.maxabs + l, T.mom_exp + l, T.mhi[l], T.mlo[l],
+                                      plan.err_flag);
         DFDM_COUNT_LAUNCH(plan);
       }
       M2lArgs a;

@@ -60,3 +60,19 @@ def test_tc_matches_fp64_form_and_is_deterministic():
     print("TC vs FP64 form rel l2 = %.3e" % err)
     assert err < TOL_TC
     assert rel_l2(yb, ya) < 1e-6
+
+
+def test_non_finite_input_reports_numeric_error():
+    t = uniform_points(3000, 71)
+    s = uniform_points(3000, 72)
+    x = complex_normal(3000, 73).astype(np.complex64)
+    x[5] = np.nan
+    with pkg.Plan(t, s, 20.0, order=4, max_depth=3, precision=pkg.TC_FP16X3) as p:
+        gpu_apply(p, x)
+        with pytest.raises(pkg.DFDMError) as e:
+            p.check()
+        assert e.value.status == 5          # DFDM_ERR_NUMERIC
+        # the check clears the word; a finite input runs clean again
+        y = gpu_apply(p, complex_normal(3000, 74).astype(np.complex64))
+        p.check()
+        assert np.all(np.isfinite(y))

@@ -1,0 +1,27 @@
+"""The stored oracle rows (tests/golden/*_rows.npz) still belong to the
+workloads they were written for: the row indices are the seeded sample, the
+exact direct-sum values are recomputed here by the oracle, and the stored
+fast-method values sit within the method's approximation error of them."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.direct import direct_rows
+from oracle.fdm import default_l_hf
+from paper_2004_14229_gb300.workloads import sample_rows, workload
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("name,approx", [("uniform-1M-k64-d6-o5", 5e-3), ("uniform-4M-k128-d7-o6", 2e-3)])
+def test_golden_rows_match_workload_and_oracle(name, approx):
+    g = np.load(os.path.join(GOLDEN, "%s_rows.npz" % name))
+    t, s, x, w = workload(name)
+    rows = g["rows"]
+    assert np.array_equal(rows, sample_rows(w["n"], rows.size, seed=4))
+    assert int(g["l_hf"]) == default_l_hf(w["kappa"], 1.0, w["depth"])
+    y = direct_rows(t, s, w["kappa"], x, rows)
+    assert np.allclose(y, g["y_direct"], rtol=1e-12, atol=0)
+    err = np.linalg.norm(g["y_fdm"] - y) / np.linalg.norm(y)
+    assert 1e-6 < err < approx          # an approximation, not a copy of the direct sum

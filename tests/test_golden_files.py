@@ -25,3 +25,18 @@ def test_golden_rows_match_workload_and_oracle(name, approx):
     assert np.allclose(y, g["y_direct"], rtol=1e-12, atol=0)
     err = np.linalg.norm(g["y_fdm"] - y) / np.linalg.norm(y)
     assert 1e-6 < err < approx          # an approximation, not a copy of the direct sum
+
+
+def test_golden_writer_runs_on_the_small_workload(tmp_path):
+    import subprocess
+    import sys
+    script = os.path.join(GOLDEN, "make_golden.py")
+    r = subprocess.run([sys.executable, script, "uniform-8k-k16-d4-o4", "6", str(tmp_path)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    g = np.load(str(tmp_path / "uniform-8k-k16-d4-o4_rows.npz"))
+    t, s, x, w = workload("uniform-8k-k16-d4-o4")
+    assert np.array_equal(g["rows"], sample_rows(w["n"], 6, seed=4))
+    assert np.allclose(g["y_direct"], direct_rows(t, s, w["kappa"], x, g["rows"]), rtol=1e-12, atol=0)
+    err = np.linalg.norm(g["y_fdm"] - g["y_direct"]) / np.linalg.norm(g["y_direct"])
+    assert err < 1e-2

@@ -231,6 +231,19 @@ dfdm_status dfdm_direct_rows_noalloc(const double *targets, int64_t n_t,
 /* Frees the plan and everything it owns; NULL is allowed. */
 dfdm_status dfdm_plan_destroy(dfdm_plan plan);
 
+/* Counts of the block partition (Alg. 2) for a uniform tree of depth
+ * `depth` whose every box is occupied on both sides -- Sect. 4's tensor grid
+ * with n_max = 512 is one -- from the planner's per-level offset tables alone
+ * (host only: no points, no GPU): *n_coupling = N_C (admissible blocks of
+ * Alg. 2), *n_stored_coupling = N_SC (distinct (level, offset) coupling
+ * matrices), *near_leaf_pairs = inadmissible leaf pairs (nearfield blocks).
+ * root_side = side of the root cube; l_hf: -2 = the default rule.  Any output
+ * pointer may be NULL.  Errors: INVALID_ARG. */
+dfdm_status dfdm_uniform_counts(double kappa, double eta2, double root_side,
+                                int depth, int l_hf, int64_t *n_coupling,
+                                int64_t *n_stored_coupling,
+                                int64_t *near_leaf_pairs);
+
 /* ---------------------------------------------------------------- batches
  * Many independent products, each of Sect. 2 for its own P_T, P_S and kappa
  * (the paper treats one problem at a time; the batched form is this

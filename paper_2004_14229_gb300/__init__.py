@@ -29,7 +29,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_batch_create", "dfdm_batch_apply", "dfdm_batch_check", "dfdm_batch_plan",
     "dfdm_batch_info", "dfdm_batch_destroy",
     "dfdm_selector_param_count", "dfdm_selector_features", "dfdm_selector_forward",
-    "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params",
+    "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params", "dfdm_uniform_counts",
 ]
 
 
@@ -108,6 +108,8 @@ def load_library():
         "dfdm_selector_grad": [vp, vp, vp, i64, vp, vp, vp],
         "dfdm_selector_train": [vp, vp, vp, i64, i32, ctypes.c_float, vp, vp, vp],
         "dfdm_select_params": [vp, dbl, dbl, i64, ctypes.POINTER(Params), vp],
+        "dfdm_uniform_counts": [dbl, dbl, dbl, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                ctypes.POINTER(i64)],
         "dfdm_last_error": [],
         "dfdm_version": [],
     }
@@ -136,6 +138,17 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def uniform_counts(kappa, depth, eta2=5.0, root_side=1.0, l_hf=None):
+    """(N_C, N_SC, nearfield leaf pairs) of Alg. 2 for a uniform tree whose
+    every box is occupied (dfdm_uniform_counts; host only, no GPU)."""
+    lib = load_library()
+    nc, ns, npr = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.dfdm_uniform_counts(float(kappa), float(eta2), float(root_side), int(depth),
+                                   -2 if l_hf is None else int(l_hf), ctypes.byref(nc), ctypes.byref(ns),
+                                   ctypes.byref(npr)))
+    return nc.value, ns.value, npr.value
 
 
 def direct_rows(targets, sources, kappa, x, rows, stream=None, y=None, noalloc=False):

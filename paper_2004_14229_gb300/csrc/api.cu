@@ -418,6 +418,52 @@ dfdm_status dfdm_plan_destroy(dfdm_plan plan) {
   return DFDM_OK;
 }
 
+dfdm_status dfdm_uniform_counts(double kappa, double eta2, double root_side, int depth, int l_hf,
+                                int64_t *n_coupling, int64_t *n_stored_coupling, int64_t *near_leaf_pairs) {
+  if (!(kappa > 0) || !std::isfinite(kappa) || !(eta2 > 0) || !std::isfinite(eta2) || !(root_side > 0) ||
+      !std::isfinite(root_side) || depth < 0 || depth > kMaxDepth || l_hf < -2)
+    return fail(DFDM_ERR_INVALID_ARG, "dfdm_uniform_counts: invalid argument");
+  return guarded([&]() -> dfdm_status {
+    Plan plan;   // host tables only: no trees, no device memory
+    plan.kappa = kappa;
+    plan.params.eta2 = eta2;
+    plan.root_side = root_side;
+    plan.depth = depth;
+    plan.l_hf = (l_hf == -2) ? default_l_hf(kappa, root_side, depth) : l_hf;
+    if (plan.l_hf > depth) plan.l_hf = depth;
+    build_levels(plan);
+    // targets t of parity a on a grid of g boxes per axis whose source t - d
+    // is on the grid too
+    auto cnt = [](int64_t g, int a, int64_t d) -> int64_t {
+      const int64_t lo = std::max<int64_t>(0, d), hi = std::min<int64_t>(g, g + d);
+      if (hi <= lo) return 0;
+      const int64_t first = lo + (((a - lo) % 2) + 2) % 2;
+      return first >= hi ? 0 : (hi - 1 - first) / 2 + 1;
+    };
+    int64_t nc = 0;
+    for (int l = 1; l <= depth; ++l) {
+      const LevelPlan &L = plan.levels[l];
+      for (int alpha = 0; alpha < 8; ++alpha)
+        for (int op : L.alpha_ops[alpha]) {
+          int64_t c = 1;
+          for (int i = 0; i < 3; ++i) c *= cnt(L.grid, (alpha >> i) & 1, L.off[3 * op + i]);
+          nc += c;
+        }
+    }
+    int64_t np = 0;
+    const int64_t g = (int64_t)1 << depth;
+    for (size_t i = 0; i + 2 < plan.near_off.size(); i += 3) {
+      int64_t c = 1;
+      for (int k = 0; k < 3; ++k) c *= std::max<int64_t>(0, g - std::abs((int64_t)plan.near_off[i + k]));
+      np += c;
+    }
+    if (n_coupling) *n_coupling = nc;
+    if (n_stored_coupling) *n_stored_coupling = plan.n_ops;
+    if (near_leaf_pairs) *near_leaf_pairs = np;
+    return DFDM_OK;
+  });
+}
+
 const char *dfdm_last_error(void) { return last_error(); }
 
 const char *dfdm_version(void) { return "dfdm-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,37 @@
+"""The library's planner (csrc/planner.cu, host code) against Table 1 of
+Sect. 4, all five printed rows k = 5..9: on the tensor grid with n_max = 512
+every box of the depth-(k-3) uniform tree is occupied, so N_C, N_SC and the
+nearfield share follow from the planner's per-level offset tables alone
+(dfdm_uniform_counts, no points, no GPU).  The oracle's own block tree pins
+k = 5..7 in test_oracle_blocktree.py; k = 8, 9 (1.7e7 and 1.3e8 points) are
+checked only here."""
+import json
+import os
+
+import pytest
+
+import paper_2004_14229_gb300 as pkg
+
+TABLE = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1.json")))
+
+
+@pytest.mark.parametrize("k", [5, 6, 7, 8, 9])
+def test_table1_counts_from_the_planner(k):
+    row = TABLE["rows"][str(k)]
+    # root [-1, 1]^3 (side 2), depth k - 3, kappa = 0.1 2^k, eta2 = 5, l_hf = k - 4
+    nc, nsc, near = pkg.uniform_counts(row["kappa"], k - 3, eta2=5.0, root_side=2.0, l_hf=k - 4)
+    assert nc == row["N_C"]
+    assert nsc == row["N_SC"]
+    leaf_points = 512
+    nf = 100.0 * near * leaf_points ** 2 / float(row["N"]) ** 2
+    digits = len(str(row["nf_percent"]).split(".")[1])
+    assert round(nf, digits) == pytest.approx(row["nf_percent"]), nf
+    # the default high-frequency rule gives the same partition (reading R12: l_hf = k - 4)
+    assert pkg.uniform_counts(row["kappa"], k - 3, eta2=5.0, root_side=2.0) == (nc, nsc, near)
+
+
+def test_uniform_counts_rejects_bad_arguments():
+    for args in ((0.0, 3), (1.0, -1), (1.0, 11)):
+        with pytest.raises(pkg.DFDMError) as e:
+            pkg.uniform_counts(*args)
+        assert e.value.status == 1

@@ -244,6 +244,16 @@ dfdm_status dfdm_uniform_counts(double kappa, double eta2, double root_side,
                                 int64_t *n_stored_coupling,
                                 int64_t *near_leaf_pairs);
 
+/* The coupling structure of one level of such a uniform tree, in the format
+ * of dfdm_plan_export_offsets (offsets d = t - s and direction indices for
+ * targets of parity alpha_index), from the planner alone (host only).
+ * Errors: INVALID_ARG (arguments as dfdm_uniform_counts, level outside
+ * 0..depth, alpha_index outside 0..7, *count too small). */
+dfdm_status dfdm_uniform_offsets(double kappa, double eta2, double root_side,
+                                 int depth, int l_hf, int level,
+                                 int alpha_index, int32_t *count,
+                                 int32_t *offsets, int32_t *dirs);
+
 /* ---------------------------------------------------------------- batches
  * Many independent products, each of Sect. 2 for its own P_T, P_S and kappa
  * (the paper treats one problem at a time; the batched form is this

@@ -30,6 +30,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_batch_info", "dfdm_batch_destroy",
     "dfdm_selector_param_count", "dfdm_selector_features", "dfdm_selector_forward",
     "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params", "dfdm_uniform_counts",
+    "dfdm_uniform_offsets",
 ]
 
 
@@ -110,6 +111,7 @@ def load_library():
         "dfdm_select_params": [vp, dbl, dbl, i64, ctypes.POINTER(Params), vp],
         "dfdm_uniform_counts": [dbl, dbl, dbl, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                 ctypes.POINTER(i64)],
+        "dfdm_uniform_offsets": [dbl, dbl, dbl, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, vp],
         "dfdm_last_error": [],
         "dfdm_version": [],
     }
@@ -149,6 +151,22 @@ def uniform_counts(kappa, depth, eta2=5.0, root_side=1.0, l_hf=None):
                                    -2 if l_hf is None else int(l_hf), ctypes.byref(nc), ctypes.byref(ns),
                                    ctypes.byref(npr)))
     return nc.value, ns.value, npr.value
+
+
+def uniform_offsets(kappa, depth, level, alpha, eta2=5.0, root_side=1.0, l_hf=None):
+    """(offsets (k, 3) int32, direction indices (k,)) of Alg. 2's admissible
+    leaves on `level` for targets of parity alpha, for a fully occupied uniform
+    tree (dfdm_uniform_offsets; host only)."""
+    lib = load_library()
+    lh = -2 if l_hf is None else int(l_hf)
+    cnt = ctypes.c_int32(0)
+    _check(lib.dfdm_uniform_offsets(float(kappa), float(eta2), float(root_side), int(depth), lh, int(level),
+                                    int(alpha), ctypes.byref(cnt), None, None))
+    off = np.empty((cnt.value, 3), dtype=np.int32)
+    dirs = np.empty(cnt.value, dtype=np.int32)
+    _check(lib.dfdm_uniform_offsets(float(kappa), float(eta2), float(root_side), int(depth), lh, int(level),
+                                    int(alpha), ctypes.byref(cnt), off.ctypes.data, dirs.ctypes.data))
+    return off, dirs
 
 
 def direct_rows(targets, sources, kappa, x, rows, stream=None, y=None, noalloc=False):

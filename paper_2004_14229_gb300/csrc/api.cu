@@ -418,20 +418,56 @@ dfdm_status dfdm_plan_destroy(dfdm_plan plan) {
   return DFDM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+bool uniform_args_ok(double kappa, double eta2, double root_side, int depth, int l_hf) {
+  return kappa > 0 && std::isfinite(kappa) && eta2 > 0 && std::isfinite(eta2) && root_side > 0 &&
+         std::isfinite(root_side) && depth >= 0 && depth <= kMaxDepth && l_hf >= -2;
+}
+// The planner's tables of a uniform tree (host only: no trees, no device memory).
+void uniform_plan(Plan &plan, double kappa, double eta2, double root_side, int depth, int l_hf) {
+  plan.kappa = kappa;
+  plan.params.eta2 = eta2;
+  plan.root_side = root_side;
+  plan.depth = depth;
+  plan.l_hf = (l_hf == -2) ? default_l_hf(kappa, root_side, depth) : l_hf;
+  if (plan.l_hf > depth) plan.l_hf = depth;
+  build_levels(plan);
+}
+}  // namespace
+
+extern "C" {
+
+dfdm_status dfdm_uniform_offsets(double kappa, double eta2, double root_side, int depth, int l_hf, int level,
+                                 int alpha_index, int32_t *count, int32_t *offsets, int32_t *dirs) {
+  if (!count || !uniform_args_ok(kappa, eta2, root_side, depth, l_hf) || level < 0 || level > depth ||
+      alpha_index < 0 || alpha_index > 7)
+    return fail(DFDM_ERR_INVALID_ARG, "dfdm_uniform_offsets: invalid argument");
+  return guarded([&]() -> dfdm_status {
+    Plan plan;
+    uniform_plan(plan, kappa, eta2, root_side, depth, l_hf);
+    const LevelPlan &L = plan.levels[level];
+    const auto &ops = L.alpha_ops[alpha_index];
+    if (offsets) {
+      if (*count < (int32_t)ops.size()) return fail(DFDM_ERR_INVALID_ARG, "*count too small");
+      for (size_t i = 0; i < ops.size(); ++i) {
+        for (int a = 0; a < 3; ++a) offsets[3 * i + a] = L.off[3 * ops[i] + a];
+        if (dirs) dirs[i] = L.op_dir[ops[i]];
+      }
+    }
+    *count = (int32_t)ops.size();
+    return DFDM_OK;
+  });
+}
+
 dfdm_status dfdm_uniform_counts(double kappa, double eta2, double root_side, int depth, int l_hf,
                                 int64_t *n_coupling, int64_t *n_stored_coupling, int64_t *near_leaf_pairs) {
-  if (!(kappa > 0) || !std::isfinite(kappa) || !(eta2 > 0) || !std::isfinite(eta2) || !(root_side > 0) ||
-      !std::isfinite(root_side) || depth < 0 || depth > kMaxDepth || l_hf < -2)
+  if (!uniform_args_ok(kappa, eta2, root_side, depth, l_hf))
     return fail(DFDM_ERR_INVALID_ARG, "dfdm_uniform_counts: invalid argument");
   return guarded([&]() -> dfdm_status {
-    Plan plan;   // host tables only: no trees, no device memory
-    plan.kappa = kappa;
-    plan.params.eta2 = eta2;
-    plan.root_side = root_side;
-    plan.depth = depth;
-    plan.l_hf = (l_hf == -2) ? default_l_hf(kappa, root_side, depth) : l_hf;
-    if (plan.l_hf > depth) plan.l_hf = depth;
-    build_levels(plan);
+    Plan plan;
+    uniform_plan(plan, kappa, eta2, root_side, depth, l_hf);
     // targets t of parity a on a grid of g boxes per axis whose source t - d
     // is on the grid too
     auto cnt = [](int64_t g, int a, int64_t d) -> int64_t {

@@ -35,3 +35,33 @@ def test_uniform_counts_rejects_bad_arguments():
         with pytest.raises(pkg.DFDMError) as e:
             pkg.uniform_counts(*args)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("k,depth,kappa", [(4, 3, 6.0), (4, 3, 40.0), (4, 4, 8.0)])
+def test_offset_tables_match_the_oracle_block_tree(k, depth, kappa):
+    """Every (offset, direction) the planner lists for a target box of the
+    fully occupied grid is an admissible block of the oracle's Alg. 2 with
+    the direction of Def. 3, and nothing is missing (bit-exact)."""
+    from oracle.fdm import FDMOracle
+    from paper_2004_14229_gb300.workloads import tensor_grid
+    pts = tensor_grid(k)                     # 8^k points: every box down to depth k occupied
+    o = FDMOracle(pts, pts, kappa, 2, [-1.0, -1.0, -1.0], 2.0, depth)
+    tt, ts = o.tt, o.ts
+    assert all(len(tt.by_level[lv]) == 8 ** lv for lv in range(depth + 1))
+    want = {}
+    for (t, s) in o.block_tree().adm:
+        d = tuple(int(v) for v in (tt.ijk[t] - ts.ijk[s]))
+        want.setdefault(t, set()).add((d, o.c_of_block(t, s)))
+    for lv in range(1, depth + 1):
+        tables = [pkg.uniform_offsets(kappa, depth, lv, a, root_side=2.0, l_hf=o.l_hf) for a in range(8)]
+        for t in tt.by_level[lv]:
+            ijk = tt.ijk[t]
+            alpha = int(ijk[0] & 1) + 2 * int(ijk[1] & 1) + 4 * int(ijk[2] & 1)
+            off, dirs = tables[alpha]
+            got = set()
+            g = 1 << lv
+            for d, c in zip(off, dirs):
+                s_ijk = ijk - d
+                if all(0 <= v < g for v in s_ijk):
+                    got.add((tuple(int(v) for v in d), int(c)))
+            assert got == want.get(t, set()), (lv, t)

@@ -65,3 +65,24 @@ def test_offset_tables_match_the_oracle_block_tree(k, depth, kappa):
                 if all(0 <= v < g for v in s_ijk):
                     got.add((tuple(int(v) for v in d), int(c)))
             assert got == want.get(t, set()), (lv, t)
+
+
+@pytest.mark.parametrize("k", [6, 7, 8])
+def test_direction_indices_within_the_direction_sets(k):
+    """Alg. 3: level l <= l_hf has 6 4^(l_hf - l) directions, coarser levels
+    none (index 0); every coupling offset's direction index is in range and
+    the finest high-frequency level uses all six faces."""
+    kappa, depth, lhf = 0.1 * 2 ** k, k - 3, k - 4
+    for lv in range(1, depth + 1):
+        used = set()
+        for a in range(8):
+            _, dirs = pkg.uniform_offsets(kappa, depth, lv, a, root_side=2.0, l_hf=lhf)
+            used.update(int(c) for c in dirs)
+        if not used:              # no admissible block on this level (the coarsest ones)
+            continue
+        if lv <= lhf:
+            assert max(used) < 6 * 4 ** (lhf - lv) and min(used) >= 0, lv
+        else:
+            assert used == {0}, lv
+        if lv == lhf:
+            assert used == set(range(6))

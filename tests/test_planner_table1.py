@@ -8,6 +8,7 @@ checked only here."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import paper_2004_14229_gb300 as pkg
@@ -86,3 +87,38 @@ def test_direction_indices_within_the_direction_sets(k):
             assert used == {0}, lv
         if lv == lhf:
             assert used == set(range(6))
+
+
+def _adm(d, level, kappa, eta2, side):
+    """(A1) and (A3) of Def. 1 for boxes of `level` at integer offset d, by the oracle."""
+    from oracle.fdm import admissibility
+    w = side / 2 ** level
+    lo_t = [0.0, 0.0, 0.0]
+    hi_t = [w, w, w]
+    lo_s = [-d[i] * w for i in range(3)]
+    hi_s = [lo_s[i] + w for i in range(3)]
+    a1, a3 = admissibility(lo_t, hi_t, lo_s, hi_s, kappa, eta2)
+    return a1 and a3
+
+
+def test_offsets_are_alg2_leaves_for_random_parameters():
+    """For random kappa, eta2, root side and depth: every listed offset d is
+    admissible on its level (Def. 1 by the oracle) and its parent pair, whose
+    offset is ceil((d - alpha) / 2), is not -- the leaves of Alg. 2 -- and
+    the counts agree with the tables."""
+    rng = np.random.default_rng(17)
+    for _ in range(12):
+        kappa = float(np.exp(rng.uniform(np.log(1.0), np.log(60.0))))
+        eta2 = float(rng.choice([2.0, 5.0, 8.0]))
+        side = float(rng.choice([1.0, 2.0]))
+        depth = int(rng.integers(2, 5))
+        for lv in range(1, depth + 1):
+            for alpha in range(8):
+                off, _ = pkg.uniform_offsets(kappa, depth, lv, alpha, eta2=eta2, root_side=side)
+                al = [(alpha >> i) & 1 for i in range(3)]
+                if len(off) > 40:                    # a random sample keeps the test short
+                    off = off[rng.choice(len(off), 40, replace=False)]
+                for d in off:
+                    assert _adm(d, lv, kappa, eta2, side), (kappa, eta2, side, lv, tuple(d))
+                    dp = [-((al[i] - int(d[i])) // 2) for i in range(3)]
+                    assert not _adm(dp, lv - 1, kappa, eta2, side), (kappa, eta2, side, lv, tuple(d))

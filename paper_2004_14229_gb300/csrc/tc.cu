@@ -1,30 +1,33 @@
 // Tensor-core form of Alg. 4 (DFDM_TC_FP16X3).
 //
 // M2L, the dense complex contraction g~_t += A~_d v~_{t-d} over all
-// admissible offsets d (Sect. 2.6, multiplication phase), runs on the tcgen05
-// tensor cores:
+// admissible offsets d (Sect. 2.6, multiplication phase; one stored operator
+// per level and offset, Sect. 2.7), runs on the tcgen05 tensor cores
+// (k_m2l_pair):
 //   * complex n x n products are real-stacked: outputs [Re; Im] (rows) times
-//     inputs [Re v; Im v] (K), each padded to NP = KP (a multiple of 32);
-//   * each FP32 operand value a is split into two FP16 terms a = a_hi + a_lo
-//     (a_hi = fp16(a), a_lo = fp16(a - a_hi)) after a power-of-two scale per
-//     level, and the product takes a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32
+//     inputs [Re v; Im v] (K), each padded to NP = KP (a multiple of 64);
+//   * each value a is split into two FP16 terms a = a_hi + a_lo (a_hi =
+//     fp16(a), a_lo = fp16(a - a_hi)) after a power-of-two scale per level,
+//     and the product takes a_hi b_hi + a_lo b_hi + a_hi b_lo with FP32
 //     accumulation in TMEM (the dropped a_lo b_lo is ~2^-22 relative);
-//   * one CTA owns 128 targets of one parity alpha (a 8 x 4 x 4 block of the
-//     parent grid) and walks the level's offset list for alpha; the source
-//     moments of all 128 targets for offset d are one TMA box with element
-//     stride 2 in x, y, z over the dense moment grid, so out-of-grid sources
-//     arrive as zeros;
-//   * the accumulator (128 targets x NP outputs, FP32) lives in TMEM; it is
-//     drained into the FP32 local grid by four epilogue warps every time the
-//     direction slot changes and every kFlushOps offsets, so no FP32 chain in
-//     TMEM grows longer than kFlushOps * 3 * KP / 16 MMA steps.
-// Warp roles: warp 0 issues TMA loads, warp 1 issues MMAs (and owns TMEM),
-// warps 2-5 drain TMEM.  Every wait is bounded; a wait that gives up sets the
-// plan's error word (read by dfdm_plan_check) and the CTA leaves its loop.
+//   * a cluster of two CTAs owns 256 targets of one parity alpha (an
+//     8 x 4 x 8 block of the parent grid) and walks one chunk of the level's
+//     offset list for alpha with tcgen05.mma.cta_group::2 (M = 256, every row
+//     a target; each CTA holds half of every operator tile); the source
+//     moments of a CTA's 128 targets for offset d are one TMA box with
+//     element stride 2 in x, y, z over the dense moment grid, so out-of-grid
+//     sources arrive as zeros; each CTA's share of an operator stage is one
+//     bulk copy of its pre-swizzled image;
+//   * warp roles: 0 copies (both CTAs), 1 issues MMAs (rank 0), 2 forwards
+//     rank 1's completed stages to rank 0 (rank 1), 4-11 drain TMEM into
+//     FP32 running sums held in registers and flush them into the FP64
+//     locals.  Every wait is bounded; a wait that gives up sets the plan's
+//     error word (read by dfdm_plan_check) and both CTAs leave their loops.
 //
 // The other phases (S2M, M2M, L2L, L2T, nearfield) run in FP32 on the CUDA
-// cores with FP64 reduction of large phase arguments; moments and locals are
-// real-stacked FP32 rows [Re 0..n-1 | Im 0..n-1 | pad] of KP floats.
+// cores with FP64 reduction of large phase arguments; moments are
+// real-stacked FP32 rows [Re 0..n-1 | Im 0..n-1 | pad] of KP floats, locals
+// the same rows in FP64.
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
@@ -80,65 +83,6 @@ __device__ __forceinline__ float abs_or_inf(float v) {
 
 __device__ __forceinline__ void atomic_max_abs(float *addr, float v) {
   atomicMax(reinterpret_cast<int *>(addr), __float_as_int(fabsf(v)));
-}
-
-// ------------------------------------------------ operators (FP64 -> FP16x2)
-// Real-stacked coupling operator of (level, d), scaled by 2^e and split:
-// row j < n: [Re A[j, :], -Im A[j, :]]; row NH + j: [Im A[j, :], Re A[j, :]],
-// with NH = NP / 2 the half of the padded output rows.
-// Operator image: for each (op, output half h, K step kc) one contiguous
-// block [hi | lo], each NH rows x 16 halves (32 B) in the 32-byte swizzled
-// layout the MMA descriptors read (16-byte chunk index XOR bit 2 of the row),
-// so one untiled bulk copy moves a whole stage's operator half.
-__device__ __forceinline__ int64_t op_image_index(int64_t op, int h, int kc, int hl, int j, int e, int KSTEPS,
-                                                  int NH) {
-  const int chunk = (e >> 3) ^ ((j >> 1) & 3);
-  const int64_t tile = ((op * 2 + h) * KSTEPS + kc) * 2 + hl;
-  return tile * NH * 32 + j * 32 + chunk * 8 + (e & 7);
-}
-
-__global__ void k_coupling_split(int order, int n, int KP, int NH, const int32_t *op_level,
-                                 const int32_t *op_off, const double *op_dir, const double *level_w,
-                                 const float *level_scale, double kappa, __half *opk) {
-  const int op = blockIdx.x;   // x: up to 2^31 - 1 operators
-  const int row = blockIdx.y;  // 0 .. 2 NH - 1
-  const int l = op_level[op];
-  const double w = level_w[l], h = 0.5 * w;
-  const float sc = level_scale[l];
-  const bool im_row = row >= NH;
-  const int j = im_row ? row - NH : row;
-  const int KSTEPS = KP / 32;
-  const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
-  const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
-  for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
-    float val = 0.0f;
-    const bool kim = kk >= n;
-    const int k = kim ? kk - n : kk;
-    if (j < n && kk < 2 * n) {
-      const int jx = j % order, jy = (j / order) % order, jz = j / (order * order);
-      const int kx = k % order, ky = (k / order) % order, kz = k / (order * order);
-      const double e0 = h * (c_cheb[jx] - c_cheb[kx]);
-      const double e1 = h * (c_cheb[jy] - c_cheb[ky]);
-      const double e2 = h * (c_cheb[jz] - c_cheb[kz]);
-      const double v0 = w * d0 + e0, v1 = w * d1 + e1, v2 = w * d2 + e2;
-      const double r = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-      const double arg = kappa * (r - (e0 * c0 + e1 * c1 + e2 * c2));
-      double s, c;
-      sincos(arg, &s, &c);
-      const double inv = 1.0 / (4.0 * kPi * r);
-      const double re = c * inv, im = s * inv;
-      // real-stacked block [[Re, -Im], [Im, Re]]
-      double v;
-      if (!im_row) v = kim ? -im : re;
-      else v = kim ? re : im;
-      val = (float)(v * (double)sc);
-    }
-    const __half hi = __float2half_rn(val);
-    const __half lo = __float2half_rn(val - __half2float(hi));
-    const int kc = kk >> 5, e = kk & 31, hh = im_row ? 1 : 0;
-    opk[op_image_index(op, hh, kc, 0, j, e, KSTEPS, NH)] = hi;
-    opk[op_image_index(op, hh, kc, 1, j, e, KSTEPS, NH)] = lo;
-  }
 }
 
 // Centred directional diagonals P_{oct,c}[k] (FP64 arguments) as float2.
@@ -421,23 +365,7 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
 }
 
 // ------------------------------------------------------------- M2L (TC)
-// One CTA: 64 targets of parity alpha (a 4 x 4 x 4 block of the parent
-// grid), one level, one chunk of the operator list.  The NP stacked outputs
-// are computed in two passes, one per half of NH = NP / 2 rows (the real
-// parts, then the imaginary parts).  Per K step of 16:
-//   MMA1: A1 = [M_hi (targets 0..63); M_lo (targets 0..63)] times O_hi[half]
-//   MMA2: A2 = [zeros;                M_hi (targets 0..63)] times O_lo[half]
-// so TMEM lanes 0..63 hold H = M_hi O_hi and lanes 64..127 the cross terms
-// X = M_lo O_hi + M_hi O_lo (A1 and A2 are two windows of one smem buffer
-// [Z | M_hi | M_lo]).  The tensor core truncates its FP32 accumulator
-// towards zero after every instruction, so H never accumulates more than
-// KSTEPS / kKsplit instructions: each operator runs as kKsplit work units
-// (K parts) that alternate between two TMEM regions, and after each unit
-// eight epilogue warps add that region's H to an FP32 shared-memory sum R
-// (round to nearest) and clear it while the MMAs fill the other region.
-// X is 2^-11 of H; it is added to R every kFlushOps operators and when the
-// direction slot changes, and R then goes to the FP32 local grid.  Holding
-// R for one half only leaves room for 8 pipeline stages at order 6.
+// Arguments of one level's M2L launch.
 struct M2lArgs {
   const int32_t *alpha_ops;   // level's op list (global op indices), per alpha
   const int32_t *alpha_off;   // 9 offsets into alpha_ops
@@ -455,124 +383,194 @@ struct M2lArgs {
   int *err;                   // error word
 };
 
-constexpr int kTM = 64;                   // targets per CTA
-constexpr int kTX = 4, kTY = 4, kTZ = 4;  // parent-grid block of a CTA
 constexpr int kK = 32;                    // K per stage (64-byte rows, two MMA K steps)
-constexpr int kKsplit = 2;                // K parts (work units) per operator and half
-constexpr int kM2lWarps = 16;             // 8 H warps, 6 X warps, 6 TMA, 7 MMA
-constexpr int kTmaWarp = 6, kMmaWarp = 7;
-constexpr int kM2lThreads = kM2lWarps * 32;
-constexpr int kEpiWarps = 14;
-constexpr int kRS = kTM + 1;              // row stride of R (conflict-free both ways)
-constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr int kFlushOps = 32;
+
+// ------------------------------------------------- M2L (TC, CTA pairs)
+// One cluster of two CTAs = 256 targets of parity alpha (an 8 x 4 x 8 block
+// of the parent grid; rank 0 the lower z half, rank 1 the upper), one level,
+// one chunk of the operator list.  Every MMA is tcgen05.mma.cta_group::2 with
+// M = 256 (each CTA's 128 target rows), N = NH = NP / 2 outputs (two passes
+// over the list, real then imaginary parts; each CTA holds NH / 2 rows of the
+// operator half) and K = 16.  Per K step three products:
+//   H  = M_hi O_hi             TMEM columns [0, NH)
+//   X += M_lo O_hi + M_hi O_lo TMEM columns [256, 256 + NH)
+// so every tensor-core row carries a target and each SM reads half of every
+// operator tile.  The tensor core truncates its FP32 accumulator toward zero
+// after each instruction, so H lives for one unit of kPU stages (2 kPU
+// instructions) only: the MMAs of a unit first build H, then add the unit's
+// cross terms to X, and eight epilogue warps per CTA add H into FP32 running
+// sums R held in registers while the X instructions run.  X (2^-11 of H)
+// accumulates over a whole group of operators that share a direction slot
+// (at most kPGroupOps); at the group's end X is added to R and R goes to the
+// FP64 locals (a transposition through shared memory, then coalesced FP64
+// atomic adds).  Units may span operators of a group (H sums over K and over
+// the group's operators alike).
+//
+// Synchronisation: each CTA's copies complete on its own full barrier; in
+// rank 1 a relay thread forwards every completed stage to rank 0's full
+// barrier (count 2), where the MMA thread waits.  Commits multicast to both
+// CTAs (stage free, H ready, X ready, all done); the epilogue warps of both
+// CTAs arrive on rank 0's H-free / X-free barriers.  Every wait is bounded; a
+// wait that gives up sets the error word and the abort flag of both CTAs.
+constexpr int kPTM = 128;                  // targets per CTA
+constexpr int kPX = 8, kPY = 4, kPZ = 4;   // parent-grid block of one CTA
+constexpr int kPU = 3;                     // stages per H unit
+constexpr int kPGroupOps = 16;             // operators per group at most
+constexpr int kPWarps = 12;                // 0 producer, 1 MMA, 2 relay, 4-11 epilogue
+constexpr int kPThreads = kPWarps * 32;
+constexpr int kPEpiWarp0 = 4;
+constexpr int kPEpiThreads = 8 * 32;
+constexpr int kPBufRS = kPTM + 1;          // transposition buffer row stride (floats)
+constexpr uint32_t kPXCol = 256;           // TMEM column of X
 
 template <int NP>
-struct M2lSmem {
-  static constexpr int NH = NP / 2;
-  static constexpr int kRowB = kK * 2;                 // bytes per operand row
-  static constexpr int kZ = kTM * kRowB;               // zero rows
-  static constexpr int kM = kTM * kRowB;               // 64 moment rows
-  static constexpr int kO = NH * kRowB;                // one half of the operator rows
-  static constexpr int kOffMhi = kZ, kOffMlo = kZ + kM, kOffOhi = kZ + 2 * kM, kOffOlo = kZ + 2 * kM + kO;
-  static constexpr int kStage = kZ + 2 * kM + 2 * kO;
-  static constexpr int kTx = 2 * kM + 2 * kO;          // bytes TMA brings per stage
-  static constexpr int kR = kRS * NH * 4;              // FP32 running sums R[col][row] of one half
-  static constexpr int kStFit = (227 * 1024 - 2048 - kR) / kStage;
-  static constexpr int kSt = kStFit < 12 ? kStFit : 12;
-  static constexpr int kTotal = kSt * kStage + kR + 1024;
+struct PairSmem {
+  static constexpr int NH = NP / 2;                // N of one MMA
+  static constexpr int NB = NH / 2;                // operator rows one CTA holds
+  static constexpr int kRowB = kK * 2;             // 64-byte operand rows
+  static constexpr int kM = kPTM * kRowB;          // 128 moment rows
+  static constexpr int kO = NB * kRowB;
+  static constexpr int kOffMhi = 0, kOffMlo = kM, kOffOhi = 2 * kM, kOffOlo = 2 * kM + kO;
+  static constexpr int kStage = 2 * kM + 2 * kO;
+  static constexpr int kBuf = 16 * kPBufRS * 4;    // 16 columns x 128 targets, FP32
+  static constexpr int kStFit = (227 * 1024 - 1024 - kBuf - 512) / kStage;
+  static constexpr int kSt = kStFit < 10 ? kStFit : 10;
+  static constexpr int kTotal = kSt * kStage + kBuf + 1024;
   static_assert(kStage % 1024 == 0, "stage alignment");
-  static_assert(kOffOlo == kOffOhi + kO, "operator hi and lo tiles are one contiguous copy");
-  static_assert(kSt >= 3, "too few pipeline stages");
+  static_assert(NB % 8 == 0, "operator rows per CTA: whole 8-row swizzle atoms");
+  static_assert(kSt >= 2 * kPU + 1, "a unit's stages plus the next unit's must fit");
 };
 
-// H warps: 0, 1, 4, 5, 8, 9, 12, 13; lane quarter q = warp & 3 in {0, 1},
-// column group hi >> 1 in {0, 1, 2, 3}.  Every H warp drains every unit (both
-// TMEM regions), so each element of R has exactly one writer.  (A warp reaches
-// TMEM lanes 32 (warp % 4) ... + 31 only.)  Sixteen warps, four per SM
-// sub-partition, leave 128 registers a thread.
-__device__ __forceinline__ int h_index(int warp) {
-  return ((warp & 3) < 2 && warp < 14) ? ((warp >> 2) << 1) | (warp & 1) : -1;
+// Operator image of the pair kernel: for each (op, output half h, K step of
+// 32, CTA q) one contiguous block [hi | lo] of NB rows x 64 B in the 64-byte
+// swizzle, so each CTA's share of a stage is one bulk copy.
+__device__ __forceinline__ int64_t op_pair_index(int64_t op, int h, int kc, int j, int e, int KSTEPS, int NH,
+                                                 int hl) {
+  const int NB = NH / 2;
+  const int q = j / NB, jj = j - q * NB;
+  const int chunk = (e >> 3) ^ ((jj >> 1) & 3);
+  const int64_t blk = (((op * 2 + h) * KSTEPS + kc) * 2 + q) * 2 + hl;
+  return blk * NB * 32 + jj * 32 + chunk * 8 + (e & 7);
 }
-// X warps: 2, 3, 10, 11, 14, 15 (lane quarters 2, 3: the cross terms of
-// targets 0..31 and 32..63); column group 0, 1, 2 of three.
-__device__ __forceinline__ int x_index(int warp) {
-  switch (warp) {
-    case 2: case 3: return 0;
-    case 10: case 11: return 1;
-    case 14: case 15: return 2;
-    default: return -1;
+
+__global__ void k_coupling_split_pair(int order, int n, int KP, int NH, const int32_t *op_level,
+                                      const int32_t *op_off, const double *op_dir, const double *level_w,
+                                      const float *level_scale, double kappa, __half *opk) {
+  const int op = blockIdx.x;
+  const int row = blockIdx.y;   // 0 .. 2 NH - 1
+  const int l = op_level[op];
+  const double w = level_w[l], h = 0.5 * w;
+  const float sc = level_scale[l];
+  const bool im_row = row >= NH;
+  const int j = im_row ? row - NH : row;
+  const int KSTEPS = KP / 32;
+  const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
+  const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
+  for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
+    float val = 0.0f;
+    const bool kim = kk >= n;
+    const int k = kim ? kk - n : kk;
+    if (j < n && kk < 2 * n) {
+      const int jx = j % order, jy = (j / order) % order, jz = j / (order * order);
+      const int kx = k % order, ky = (k / order) % order, kz = k / (order * order);
+      const double e0 = h * (c_cheb[jx] - c_cheb[kx]);
+      const double e1 = h * (c_cheb[jy] - c_cheb[ky]);
+      const double e2 = h * (c_cheb[jz] - c_cheb[kz]);
+      const double v0 = w * d0 + e0, v1 = w * d1 + e1, v2 = w * d2 + e2;
+      const double r = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      const double arg = kappa * (r - (e0 * c0 + e1 * c1 + e2 * c2));
+      double s, c;
+      sincos(arg, &s, &c);
+      const double inv = 1.0 / (4.0 * kPi * r);
+      const double re = c * inv, im = s * inv;
+      double v;   // real-stacked block [[Re, -Im], [Im, Re]]
+      if (!im_row) v = kim ? -im : re;
+      else v = kim ? re : im;
+      val = (float)(v * (double)sc);
+    }
+    const __half hi = __float2half_rn(val);
+    const __half lo = __float2half_rn(val - __half2float(hi));
+    const int kc = kk >> 5, e = kk & 31, hh = im_row ? 1 : 0;
+    opk[op_pair_index(op, hh, kc, j, e, KSTEPS, NH, 0)] = hi;
+    opk[op_pair_index(op, hh, kc, j, e, KSTEPS, NH, 1)] = lo;
   }
 }
 
+// End of the group of operators starting at ii (same slot, at most kPGroupOps).
+__device__ __forceinline__ int pair_group_end(const M2lArgs &a, int ii, int i1) {
+  const int slot = a.op_slot[a.alpha_ops[ii]];
+  int jj = ii + 1;
+  while (jj < i1 && jj - ii < kPGroupOps && a.op_slot[a.alpha_ops[jj]] == slot) ++jj;
+  return jj;
+}
+
 template <int NP>
-__global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant__ CUtensorMap map_mhi,
-                                                          const __grid_constant__ CUtensorMap map_mlo,
-                                                          const M2lArgs args) {
-  using S = M2lSmem<NP>;
-  constexpr int NH = NP / 2;               // N of one MMA (<= 256)
-  constexpr int KSTEPS = NP / kK;          // K steps per operator (KP == NP)
-  constexpr int USTEPS = KSTEPS / kKsplit; // K steps per unit
-  constexpr int NCH = NH / 16;             // 16-column chunks of a half
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
+    k_m2l_pair(const __grid_constant__ CUtensorMap map_mhi, const __grid_constant__ CUtensorMap map_mlo,
+               const M2lArgs args) {
+  using S = PairSmem<NP>;
+  constexpr int NH = S::NH;
+  constexpr int NB = S::NB;
+  constexpr int KSTEPS = NP / kK;      // stages per operator and half
+  constexpr int NCH = NH / 16;         // 16-column chunks of one half
+  constexpr int CPW = NCH / 2;         // chunks per epilogue warp
   constexpr int kSt = S::kSt;
-  constexpr uint32_t kTmemCols = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
-  static_assert(NH % 16 == 0 && NH <= 256, "N half must be a multiple of 16, <= 256");
-  static_assert(KSTEPS % kKsplit == 0, "K steps must split evenly");
+  static_assert(NCH % 2 == 0, "two epilogue warps per TMEM lane quarter");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *R = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [NH][kRS]
-  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], acc_full[2], acc_empty[2], grp_done, mma_fin;
+  float *buf = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [16][kPBufRS]
+  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], h_full, h_empty, x_full, x_empty, fin_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
+  const uint32_t rank = ptx::cluster_rank();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = args.g, gp = g >> 1;
-  const int tiles_x = (gp + kTX - 1) / kTX, tiles_y = (gp + kTY - 1) / kTY;
+  const int tiles_x = (gp + kPX - 1) / kPX, tiles_y = (gp + kPY - 1) / kPY;
+  const int pt = blockIdx.x >> 1;
+  const int X0 = (pt % tiles_x) * kPX;
+  const int Y0 = ((pt / tiles_x) % tiles_y) * kPY;
+  const int Z0 = (pt / (tiles_x * tiles_y)) * (2 * kPZ) + (int)rank * kPZ;
   const int alpha = blockIdx.y;
-  const int tile = blockIdx.x;
-  const int X0 = (tile % tiles_x) * kTX;
-  const int Y0 = ((tile / tiles_x) % tiles_y) * kTY;
-  const int Z0 = (tile / (tiles_x * tiles_y)) * kTZ;
   const int ax = alpha & 1, ay = (alpha >> 1) & 1, az = (alpha >> 2) & 1;
-  // this CTA's chunk of the alpha's operator list (blockIdx.z of nsplit)
   const int a0 = args.alpha_off[alpha], na = args.alpha_off[alpha + 1] - a0;
   const int i0 = a0 + (int)(((int64_t)na * blockIdx.z) / args.nsplit);
   const int i1 = a0 + (int)(((int64_t)na * (blockIdx.z + 1)) / args.nsplit);
-  const bool shared_out = args.nsplit > 1;   // other CTAs add to the same locals
+  const int total_stages = 2 * (i1 - i0) * KSTEPS;
 
-  // zero rows of every stage and the running sums
-  for (int s = 0; s < kSt; ++s)
-    for (int i = tid; i < S::kZ / 16; i += blockDim.x)
-      reinterpret_cast<uint4 *>(smem + s * S::kStage)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < kRS * NH; i += blockDim.x) R[i] = 0.f;
-  ptx::fence_proxy_async();
   if (tid == 0) {
     for (int s = 0; s < kSt; ++s) {
-      ptx::mbar_init(&full_bar[s], 1);
+      ptx::mbar_init(&full_bar[s], rank == 0 ? 2 : 1);
       ptx::mbar_init(&empty_bar[s], 1);
     }
-    for (int r = 0; r < 2; ++r) {
-      ptx::mbar_init(&acc_full[r], 1);
-      ptx::mbar_init(&acc_empty[r], 8);
-    }
-    ptx::mbar_init(&grp_done, kEpiWarps);
-    ptx::mbar_init(&mma_fin, 1);
+    ptx::mbar_init(&h_full, 1);
+    ptx::mbar_init(&x_full, 1);
+    ptx::mbar_init(&fin_bar, 1);
+    ptx::mbar_init(&h_empty, 2 * 8);
+    ptx::mbar_init(&x_empty, 2 * 8);
     s_abort = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == kMmaWarp) {
-    ptx::tmem_alloc(&tmem_base, kTmemCols);
-    ptx::tmem_relinquish();
+  if (warp == 1) {
+    ptx::tmem_alloc_pair(&tmem_base, 512);
+    ptx::tmem_relinquish_pair();
   }
   ptx::tc_fence_before();
   __syncthreads();
+  ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem = tmem_base;
+  const uint32_t peer_abort = ptx::cluster_addr(&s_abort, rank ^ 1u);
+  auto abort_both = [&]() {
+    atomicExch(args.err, 1);
+    s_abort = 1;
+    ptx::st_cluster_u32(peer_abort, 1u);
+  };
 
-  if (warp == kTmaWarp) {
+  if (warp == 0) {
     if (lane == 0) {
-      // ------------------------------------------------ TMA producer
+      // ------------------------------------------------ producer (both CTAs)
       ptx::prefetch_tensormap(&map_mhi);
       ptx::prefetch_tensormap(&map_mlo);
       uint32_t it = 0;
@@ -588,203 +586,210 @@ __global__ void __launch_bounds__(kM2lThreads, 1) k_m2l_tc(const __grid_constant
           for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
             const int st = it % kSt;
             const uint32_t ph = (it / kSt) & 1;
-            if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
+            if (!ptx::mbar_wait_cluster(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
             uint8_t *base = smem + st * S::kStage;
-            ptx::mbar_expect_tx(&full_bar[st], S::kTx);
+            ptx::mbar_expect_tx(&full_bar[st], S::kStage);
             ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
             ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
-            ptx::bulk_load(base + S::kOffOhi, args.opk + (((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 * NH * 32,
+            ptx::bulk_load(base + S::kOffOhi,
+                           args.opk + ((((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 + rank) * 2 * NB * 32,
                            2 * S::kO, &full_bar[st]);
           }
         }
       }
-      // copies still in flight land before the CTA leaves: wait (bounded) for
-      // the last phase of every stage filled (already complete on a normal run)
+      // this CTA's copies still in flight land before it leaves (bounded;
+      // already complete on a normal run)
       for (uint32_t k = (it > (uint32_t)kSt ? it - kSt : 0u); k < it; ++k)
-        if (!ptx::mbar_wait(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
-      if (!ok) {
-        atomicExch(args.err, 1);
-        atomicExch(&s_abort, 1);
-      }
+        if (!ptx::mbar_wait_cluster(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
+      if (!ok) abort_both();
     }
-  } else if (warp == kMmaWarp) {
-    if (lane == 0) {
-      // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = ptx::idesc_f16_f32(128, NH);
-      uint32_t it = 0, groups = 0;
-      uint32_t units[2] = {0, 0};   // units issued per TMEM region
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ------------------------------------------------ MMA issuer (rank 0)
+      constexpr uint32_t idesc = ptx::idesc_f16_f32(256, NH);
+      uint32_t it = 0, hu = 0, xg = 0;
       bool ok = true;
       for (int h = 0; h < 2 && ok; ++h) {
-        int run = 0;
-        for (int ii = i0; ii < i1 && ok; ++ii) {
-          const int slot = args.op_slot[args.alpha_ops[ii]];
-          const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
-          for (int u = 0; u < kKsplit && ok; ++u) {
-            const int r = u & 1;       // TMEM region of this unit
-            if (units[r] > 0) {        // region drained by the epilogue?
-              if (!ptx::mbar_wait(&acc_empty[r], (units[r] - 1) & 1, kWaitLimit)) { ok = false; break; }
+        for (int ii = i0; ii < i1 && ok;) {
+          const int jj = pair_group_end(args, ii, i1);
+          const int ns = (jj - ii) * KSTEPS;
+          for (int u0 = 0; u0 < ns && ok; u0 += kPU) {
+            const int nst = min(kPU, ns - u0);
+            if (hu > 0 && !ptx::mbar_wait_cluster(&h_empty, (hu - 1) & 1, kWaitLimit)) { ok = false; break; }
+            for (int t = 0; t < nst && ok; ++t) {
+              const uint32_t k = it + t;
+              if (!ptx::mbar_wait_cluster(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
+            }
+            if (!ok) break;
+            ptx::tc_fence_after();
+            for (int t = 0; t < nst; ++t) {
+              const uint32_t base = ptx::smem_u32(smem + ((it + t) % kSt) * S::kStage);
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                const uint32_t o = 32u * j;
+                ptx::mma_f16_pair(tmem, ptx::sdesc_k_sw64(base + S::kOffMhi + o),
+                                  ptx::sdesc_k_sw64(base + S::kOffOhi + o), idesc, (t | j) ? 1u : 0u);
+              }
+            }
+            ptx::mma_commit_pair(&h_full);
+            if (u0 == 0 && xg > 0) {
+              if (!ptx::mbar_wait_cluster(&x_empty, (xg - 1) & 1, kWaitLimit)) { ok = false; break; }
               ptx::tc_fence_after();
             }
-            const uint32_t d = tmem + r * NH;
-            for (int ks = 0; ks < USTEPS; ++ks, ++it) {
-              const int st = it % kSt;
-              const uint32_t ph = (it / kSt) & 1;
-              if (!ptx::mbar_wait(&full_bar[st], ph, kWaitLimit)) { ok = false; break; }
-              ptx::tc_fence_after();
+            for (int t = 0; t < nst; ++t) {
+              const int st = (it + t) % kSt;
               const uint32_t base = ptx::smem_u32(smem + st * S::kStage);
 #pragma unroll
               for (int j = 0; j < 2; ++j) {
                 const uint32_t o = 32u * j;
-                const uint64_t a1 = ptx::sdesc_k_sw64(base + S::kOffMhi + o);
-                const uint64_t a2 = ptx::sdesc_k_sw64(base + o);
-                const uint32_t init = (units[r] == 0 && ks == 0 && j == 0) ? 0u : 1u;
-                ptx::mma_f16(d, a1, ptx::sdesc_k_sw64(base + S::kOffOhi + o), idesc, init);
-                ptx::mma_f16(d, a2, ptx::sdesc_k_sw64(base + S::kOffOlo + o), idesc, 1u);
+                ptx::mma_f16_pair(tmem + kPXCol, ptx::sdesc_k_sw64(base + S::kOffMlo + o),
+                                  ptx::sdesc_k_sw64(base + S::kOffOhi + o), idesc,
+                                  (u0 == 0 && t == 0 && j == 0) ? 0u : 1u);
+                ptx::mma_f16_pair(tmem + kPXCol, ptx::sdesc_k_sw64(base + S::kOffMhi + o),
+                                  ptx::sdesc_k_sw64(base + S::kOffOlo + o), idesc, 1u);
               }
-              ptx::mma_commit(&empty_bar[st]);
+              ptx::mma_commit_pair(&empty_bar[st]);
             }
-            if (!ok) break;
-            ptx::mma_commit(&acc_full[r]);
-            ++units[r];
+            it += nst;
+            ++hu;
           }
           if (!ok) break;
-          ++run;
-          if (next_slot != slot || run >= kFlushOps) {
-            // X and R are drained after this operator: wait for the epilogue
-            if (!ptx::mbar_wait(&grp_done, groups & 1, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
-            ++groups;
-            run = 0;
-          }
+          ptx::mma_commit_pair(&x_full);
+          ++xg;
+          ii = jj;
         }
       }
-      // every MMA issued has finished reading shared memory and writing TMEM
-      // before the CTA frees them (bounded; immediate on a normal run)
-      ptx::mma_commit(&mma_fin);
-      if (!ptx::mbar_wait(&mma_fin, 0, kWaitLimit)) ok = false;
-      if (!ok) {
-        atomicExch(args.err, 1);
-        atomicExch(&s_abort, 1);
-      }
+      if (!ok) abort_both();
+      // every MMA has finished with shared memory and TMEM of both CTAs
+      ptx::mma_commit_pair(&fin_bar);
     }
-  } else {
-    // ------------------------------------------------ epilogue
-    const int hi = h_index(warp);
-    const int xi = x_index(warp);
-    const bool xw = xi >= 0;
-    if (hi >= 0 || xw) {
-      const int q = warp & 3;                        // TMEM lane quarter
-      const int r = (q & 1) * 32 + lane;             // target row 0..63
-      const int64_t ncell = (int64_t)g * g * g;
-      const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
-      const int n = args.n;
-      const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-      const int gq = (hi >= 0) ? hi >> 1 : 0;   // column group of this H warp
-      const float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      uint32_t drains[2] = {0, 0};   // units drained so far, per TMEM region
-      bool stop = false;
-      for (int h = 0; h < 2 && !stop; ++h) {
-        int run = 0;
-        for (int ii = i0; ii < i1 && !stop; ++ii) {
-          const int slot = args.op_slot[args.alpha_ops[ii]];
-          const int next_slot = (ii + 1 < i1) ? args.op_slot[args.alpha_ops[ii + 1]] : -1;
-          ++run;
-          const bool group_end = (next_slot != slot) || run >= kFlushOps;
-          bool bad = false;
-          if (hi >= 0) {
-            // unit u of this operator went to TMEM region u & 1
-            for (int u = 0; u < kKsplit && !bad; ++u) {
-              const int reg = u & 1;
-              bool got = false;
-              const uint64_t t0 = ptx::global_ns();
-              for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
-                got = ptx::mbar_try_wait(&acc_full[reg], drains[reg] & 1);
-                if (!got && (t & 255) == 255 &&
-                    (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
-                  break;
-              }
-              if (!got) { bad = true; break; }
-              ++drains[reg];
-              ptx::tc_fence_after();
-#pragma unroll 1
-              for (int ch = gq; ch < NCH; ch += 4) {
-                const int c = ch * 16;
-                float v[16];
-                ptx::tmem_ld16(tmem + lane_addr + reg * NH + c, v);
-                ptx::tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) R[(c + i) * kRS + r] += v[i];
-                ptx::tmem_st16(tmem + lane_addr + reg * NH + c, zero);
-              }
-              ptx::tmem_st_wait();
-              ptx::tc_fence_before();
-              __syncwarp();
-              if (lane == 0) ptx::mbar_arrive(&acc_empty[reg]);
-            }
-          }
-          if (bad) atomicExch(args.err, 1);
-          // one decision for all epilogue warps; it also orders this
-          // operator's H drains before the X drain below
-          stop = ptx::named_bar_or(2, kEpiThreads, bad || *(volatile int *)&s_abort);
-          if (stop) break;
-          if (group_end) {
-            if (xw) {
-              // X of both regions -> R, then clear X (every unit of this
-              // operator has completed: the H warps consumed all acc_full)
-              ptx::tc_fence_after();
-#pragma unroll 1
-              for (int ch = xi; ch < NCH; ch += 3) {
-                const int c = ch * 16;
-                float v0[16], v1[16];
-                ptx::tmem_ld16(tmem + lane_addr + c, v0);
-                ptx::tmem_ld16(tmem + lane_addr + NH + c, v1);
-                ptx::tmem_ld_wait();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) R[(c + i) * kRS + r] += v0[i] + v1[i];
-                ptx::tmem_st16(tmem + lane_addr + c, zero);
-                ptx::tmem_st16(tmem + lane_addr + NH + c, zero);
-              }
-              ptx::tmem_st_wait();
-            }
-            ptx::named_bar(1, kEpiThreads);
-            if (hi >= 0) {
-              // R -> local grid (scaled), then clear R: H warp hi takes the
-              // targets rr = hi, hi + 8, ..., its lanes consecutive columns,
-              // so every update of the local grid is one coalesced row.
-#pragma unroll 1
-              for (int rr = hi; rr < kTM; rr += 8) {
-                const int jx = rr % kTX, jy = (rr / kTX) % kTY, jz = rr / (kTX * kTY);
-                const int XX = X0 + jx, YY = Y0 + jy, ZZ = Z0 + jz;
-                const bool ok_r = XX < gp && YY < gp && ZZ < gp;
-                const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
-                double *dst = args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n;
-#pragma unroll
-                for (int j = 0; j < (NH + 31) / 32; ++j) {
-                  const int c = lane + 32 * j;
-                  if (c < NH) {
-                    const float val = R[c * kRS + rr];
-                    R[c * kRS + rr] = 0.f;
-                    if (ok_r && c < n) {
-                      const double add = (double)val * (double)inv;
-                      if (shared_out) atomicAdd(dst + c, add);
-                      else dst[c] += add;
-                    }
-                  }
-                }
-              }
-            }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&grp_done);
-            run = 0;
-          }
+  } else if (warp == 2) {
+    if (lane == 0 && rank == 1) {
+      // ------------------------------------------------ relay (rank 1)
+      const uint32_t leader_full0 = ptx::cluster_addr(&full_bar[0], 0);
+      bool ok = true;
+      for (int k = 0; k < total_stages; ++k) {
+        const int st = k % kSt;
+        bool got = false;
+        const uint64_t t0 = ptx::global_ns();
+        for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
+          got = ptx::mbar_try_wait(&full_bar[st], (k / kSt) & 1);
+          if (!got && (t & 255) == 255 && (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
+            break;
         }
+        if (!got) { ok = false; break; }
+        ptx::mbar_arrive_cluster(leader_full0 + st * 8u);
+      }
+      if (!ok) abort_both();
+    }
+  } else if (warp >= kPEpiWarp0) {
+    // ------------------------------------------------ epilogue (both CTAs)
+    const int e = warp - kPEpiWarp0;          // 0..7
+    const int q = warp & 3;                   // TMEM lane quarter
+    const int ch = e >> 2;                    // column half of H / X (CPW chunks)
+    const int row = q * 32 + lane;            // this thread's target row
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    const uint32_t h_empty0 = ptx::cluster_addr(&h_empty, 0);
+    const uint32_t x_empty0 = ptx::cluster_addr(&x_empty, 0);
+    const int64_t ncell = (int64_t)g * g * g;
+    const int n = args.n;
+    const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
+    const int te = tid - kPEpiWarp0 * 32;     // 0..255
+    float R[CPW * 16];
+#pragma unroll
+    for (int i = 0; i < CPW * 16; ++i) R[i] = 0.f;
+    uint32_t hu = 0, xg = 0;
+    bool bad = false;
+    auto wait_local = [&](uint64_t *bar, uint32_t ph) {
+      const uint64_t t0 = ptx::global_ns();
+      for (uint32_t t = 0; t < kWaitLimit; ++t) {
+        if (ptx::mbar_try_wait_cluster(bar, ph)) return true;
+        if ((t & 255) == 255 && (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull)) return false;
+      }
+      return false;
+    };
+    bool stop = false;
+    for (int h = 0; h < 2 && !stop; ++h) {
+      for (int ii = i0; ii < i1 && !stop;) {
+        const int jj = pair_group_end(args, ii, i1);
+        const int slot = args.op_slot[args.alpha_ops[ii]];
+        const int ns = (jj - ii) * KSTEPS;
+        for (int u0 = 0; u0 < ns; u0 += kPU) {
+          if (!bad && !wait_local(&h_full, hu & 1)) bad = true;
+          ++hu;
+          if (bad) continue;
+          ptx::tc_fence_after();
+#pragma unroll
+          for (int c = 0; c < CPW; ++c) {
+            float v[16];
+            ptx::tmem_ld16(tmem + lane_addr + (uint32_t)((ch * CPW + c) * 16), v);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) R[c * 16 + i] += v[i];
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive_cluster(h_empty0);
+        }
+        if (!bad && !wait_local(&x_full, xg & 1)) bad = true;
+        ++xg;
+        if (!bad) {
+          ptx::tc_fence_after();
+#pragma unroll
+          for (int c = 0; c < CPW; ++c) {
+            float v[16];
+            ptx::tmem_ld16(tmem + lane_addr + kPXCol + (uint32_t)((ch * CPW + c) * 16), v);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) R[c * 16 + i] += v[i];
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive_cluster(x_empty0);
+        }
+        // one decision for all epilogue warps before the flush's barriers
+        stop = ptx::named_bar_or(2, kPEpiThreads, bad || *(volatile int *)&s_abort);
+        if (stop) break;
+        // R -> locals: 16 columns at a time through the transposition buffer
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+          if (ch == k / CPW) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              buf[i * kPBufRS + row] = R[(k % CPW) * 16 + i];
+              R[(k % CPW) * 16 + i] = 0.f;
+            }
+          }
+          ptx::named_bar(1, kPEpiThreads);
+#pragma unroll
+          for (int r8 = 0; r8 < kPTM * 16 / kPEpiThreads; ++r8) {
+            const int idx = r8 * kPEpiThreads + te;
+            const int rr = idx >> 4, cc = idx & 15;
+            const int col = k * 16 + cc;
+            const int XX = X0 + (rr & 7), YY = Y0 + ((rr >> 3) & 3), ZZ = Z0 + (rr >> 5);
+            if (col < n && XX < gp && YY < gp && ZZ < gp) {
+              const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
+              const float val = buf[cc * kPBufRS + rr];
+              atomicAdd(args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n + col, (double)val * (double)inv);
+            }
+          }
+          ptx::named_bar(1, kPEpiThreads);
+        }
+        ii = jj;
       }
     }
+    if (bad) abort_both();
+  }
+  // ------------------------------------------------ teardown (both CTAs)
+  if (warp == 1 && lane == 0) {
+    // the last commit of rank 0's MMA thread reached this CTA
+    if (!ptx::mbar_wait_cluster(&fin_bar, 0, kWaitLimit)) atomicExch(args.err, 1);
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == kMmaWarp) ptx::tmem_dealloc(tmem, kTmemCols);
+  ptx::cluster_sync();
+  ptx::tc_fence_after();
+  if (warp == 1) ptx::tmem_dealloc_pair(tmem, 512);
 }
 
 // ----------------------------------------------------------------- L2T
@@ -1192,10 +1197,10 @@ void build_tc(Plan &plan, cudaStream_t st) {
   // opt the M2L kernel into its dynamic shared memory once, here, so the
   // apply itself makes no attribute calls (it can be captured in a graph)
   switch (KP) {
-    case 64: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<64>::kTotal)); break;
-    case 128: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<128>::kTotal)); break;
-    case 256: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<256>::kTotal)); break;
-    case 448: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc<448>, cudaFuncAttributeMaxDynamicSharedMemorySize, M2lSmem<448>::kTotal)); break;
+    case 64: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_pair<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairSmem<64>::kTotal)); break;
+    case 128: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_pair<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairSmem<128>::kTotal)); break;
+    case 256: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_pair<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairSmem<256>::kTotal)); break;
+    case 448: DFDM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_pair<448>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairSmem<448>::kTotal)); break;
     default: break;
   }
   // FP32 constants
@@ -1282,7 +1287,7 @@ void build_tc(Plan &plan, cudaStream_t st) {
                                   (cuuint64_t)plan.levels[l].slot_dir.size()};
       const cuuint64_t strides[4] = {(cuuint64_t)KP * 2, (cuuint64_t)KP * 2 * gl, (cuuint64_t)KP * 2 * gl * gl,
                                      (cuuint64_t)KP * 2 * gl * gl * gl};
-      const cuuint32_t box[5] = {(cuuint32_t)kK, 2 * kTX, 2 * kTY, 2 * kTZ, 1};
+      const cuuint32_t box[5] = {(cuuint32_t)kK, 2 * kPX, 2 * kPY, 2 * kPZ, 1};
       const cuuint32_t es[5] = {1, 2, 2, 2, 1};
       encode(&T.map_mhi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mhi[l], dims, strides, box, es,
              CU_TENSOR_MAP_SWIZZLE_64B);
@@ -1323,8 +1328,8 @@ void build_tc(Plan &plan, cudaStream_t st) {
     DFDM_CUDA_TRY(cudaMemcpy(d_sc, level_scale.data(), level_scale.size() * 4, cudaMemcpyHostToDevice));
     const size_t ocnt = (size_t)nops * KP * KP * 2;
     T.opk = plan.alloc<__half>(ocnt);
-    k_coupling_split<<<dim3(nops, KP), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
-                                                      d_sc, plan.kappa, T.opk);
+    k_coupling_split_pair<<<dim3(nops, KP), 128, 0, st>>>(o, n, KP, KP / 2, d_level, plan.op_off_dev, d_dir, d_w,
+                                                           d_sc, plan.kappa, T.opk);
     DFDM_LAUNCH_CHECK();
     DFDM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_level);
@@ -1401,13 +1406,13 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.op_exp = T.op_exp[l];
       a.err = plan.err_flag;
       const int gp = L.grid / 2;
-      const int tiles = ((gp + kTX - 1) / kTX) * ((gp + kTY - 1) / kTY) * ((gp + kTZ - 1) / kTZ);
+      const int pairs = ((gp + kPX - 1) / kPX) * ((gp + kPY - 1) / kPY) * ((gp + 2 * kPZ - 1) / (2 * kPZ));
       size_t ops_alpha = 0;
       for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
-      a.nsplit = m2l_split(tiles, (int)ops_alpha, T.num_sms, (size_t)KP * KP * 4, T.l2_bytes);
-      const int smem = M2lSmem<NP>::kTotal;
+      a.nsplit = m2l_split(pairs, (int)ops_alpha, T.num_sms / 2, (size_t)KP * KP * 4, T.l2_bytes);
+      const int smem = PairSmem<NP>::kTotal;
       PhaseScope sc(tm, kPhM2L0 + l, st);
-      k_m2l_tc<NP><<<dim3(tiles, 8, a.nsplit), kM2lThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
+      k_m2l_pair<NP><<<dim3(2 * pairs, 8, a.nsplit), kPThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
       DFDM_COUNT_LAUNCH(plan);
     }
     {

@@ -13,8 +13,10 @@ built once before the timed region.  Prints one JSON line.
 Eq. (1) (plain C, OpenMP over the host cores) on a bounded sample of target
 rows per step, scaled to the whole product.
 
-With torchrun (N > 1) every rank runs an independent replica of the workload
-(the product is not sharded); the value is the total over all ranks.
+With --gpus N > 1 every rank (one process per GPU: started by torchrun, or by
+bench.py itself through torch.distributed.run when no launcher set WORLD_SIZE)
+runs an independent replica of the workload (the product is not sharded); the
+value is the total over all ranks.
 
 --batch P times the batched form instead: P independent problems (N
 log-uniform in [1e4, 1e6], kappa log-uniform in [8, 256], uniform / Gaussian /
@@ -444,6 +446,22 @@ def run_batch(args):
     return 0
 
 
+def _free_port():
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def launch_replicas(nproc, argv):
+    """`--gpus N` without a launcher: run this script as N ranks (one per GPU,
+    torch.distributed.run on 127.0.0.1) and return the launcher's exit code;
+    rank 0 prints the JSON line."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(nproc),
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.abspath(__file__), *argv]
+    return subprocess.run(cmd).returncode
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,6 +474,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_replicas(args.gpus, sys.argv[1:])
+    world, _, _ = _dist()
+    if args.gpus != world:
+        raise SystemExit("--gpus %d but %d ranks were launched" % (args.gpus, world))
     if args.impl == "reference":
         return run_reference(args)
     if args.batch > 0:

@@ -51,12 +51,18 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 // Bounded wait on phase `parity`: false after max_iter failed tries or once
-// more than ~1 s of wall time has passed, whichever comes first.
+// more than ~1 s of wall time has passed, whichever comes first.  The wall
+// clock (%globaltimer, slow to read) is first read after 256 failed tries,
+// so a wait whose phase is already complete costs one try_wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_iter) {
-  const uint64_t t0 = global_ns();
+  uint64_t t0 = 0;
   for (uint32_t i = 0; i < max_iter; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > 1000000000ull) return false;
+    if ((i & 255) == 255) {
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > 1000000000ull) return false;
+    }
   }
   return false;
 }
@@ -206,32 +212,29 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
   return r;
 }
-// Arrive (release at cluster scope) on a barrier given by its cluster address.
+// Arrive on a barrier given by its cluster address (possibly the other CTA's).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+// Tile loads of a CTA pair: the data land in this CTA's shared memory, the
+// completed bytes count on the barrier at cluster address `bar` (rank 0's).
+__device__ __forceinline__ void tma_load_5d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                                 int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
+      "%4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
 }
 __device__ __forceinline__ void st_cluster_u32(uint32_t cl_addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cl_addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
-      "p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait (acquire at cluster scope: the arrivals may come from the
-// other CTA); false after max_iter tries or ~1 s.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, uint32_t max_iter) {
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < max_iter; ++i) {
-    if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > 1000000000ull) return false;
-  }
-  return false;
 }
 // One warp of EACH CTA of the pair executes these (collective allocation of
 // the same columns in both CTAs' TMEM).

@@ -333,8 +333,13 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const double *ploc, double *clo
 }
 
 // ------------------------------------------------ FP32 -> FP16 hi/lo split
-__global__ void k_split(const float *src, int64_t count, const float *maxabs, int *exp_out, __half *hi,
-                        __half *lo, int *err) {
+// Source: FP32 moments [slot][cell][KP] (cell = x + G y + G^2 z).  Target:
+// the parity-split layout the M2L tiles read,
+//   [slot][K step of 32][parity (x&1) + 2 (y&1) + 4 (z&1)][z/2][y/2][x/2][32],
+// in which the moments of the eight x-neighbours of one parity that a tile
+// row needs for one K step are 512 contiguous bytes.
+__global__ void k_split(const float *src, int64_t count, int g, int KP, const float *maxabs, int *exp_out,
+                        __half *hi, __half *lo, int *err) {
   // scale 2^e with max * 2^e <= 2^14; a level maximum that is not finite, or
   // that the clamped scale cannot bring into FP16's normal range, is a
   // numeric error (error word 2, kept if an earlier error is already there)
@@ -355,12 +360,24 @@ __global__ void k_split(const float *src, int64_t count, const float *maxabs, in
     if (bad) atomicCAS(err, 0, 2);
   }
   const float sc = ldexpf(1.0f, e);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = src[i] * sc;
-    const __half h = __float2half_rn(v);
-    hi[i] = h;
-    lo[i] = __float2half_rn(v - __half2float(h));
+  // one warp per moment row (slot, cell); lane = position in a K step of 32
+  const int hg = g >> 1, ksteps = KP >> 5;
+  const int64_t ncell = (int64_t)g * g * g, nrows = count / KP;
+  const int64_t kstride = (int64_t)8 * hg * hg * hg * 32;   // one K step further
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t cell = r % ncell, slot = r / ncell;
+    const int x = (int)(cell % g), y = (int)((cell / g) % g), z = (int)(cell / ((int64_t)g * g));
+    const int par = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+    const int64_t d0 = (((((slot * ksteps) * 8 + par) * hg + (z >> 1)) * hg + (y >> 1)) * hg + (x >> 1)) * 32 + lane;
+    const float *row = src + r * KP;
+    for (int kc = 0; kc < ksteps; ++kc) {
+      const float v = row[kc * 32 + lane] * sc;
+      const __half h = __float2half_rn(v);
+      hi[d0 + kc * kstride] = h;
+      lo[d0 + kc * kstride] = __float2half_rn(v - __half2float(h));
+    }
   }
 }
 
@@ -371,15 +388,14 @@ struct M2lArgs {
   const int32_t *alpha_off;   // 9 offsets into alpha_ops
   const int32_t *op_off;      // 3 ints per global op
   const int32_t *op_slot;     // slot per global op
-  const __half *opk;          // operator images of the level (first op = op_base)
-  int op_base;                // first global op of the level
   double *loc;                // locals [slot][cell][KP], FP64 sums of FP32 partial sums
   int g;                      // level grid
   int n;                      // nodes per box
   int KP;                     // padded stacked length (= NP)
   const int *mom_exp;         // moment scale exponent of the level (device)
   int op_exp;                 // operator scale exponent of the level
-  int nsplit;                 // CTAs per (tile, alpha), each a contiguous chunk of the op list
+  const int4 *meta;           // per list entry: {op, packed offset, slot, end of its slot run}
+  int nsplit;                 // clusters per (tile, alpha), each a contiguous chunk of the op list
   int *err;                   // error word
 };
 
@@ -399,28 +415,31 @@ constexpr uint32_t kWaitLimit = 1u << 24;
 // operator tile.  The tensor core truncates its FP32 accumulator toward zero
 // after each instruction, so H lives for one unit of kPU stages (2 kPU
 // instructions) only: the MMAs of a unit first build H, then add the unit's
-// cross terms to X, and eight epilogue warps per CTA add H into FP32 running
-// sums R held in registers while the X instructions run.  X (2^-11 of H)
-// accumulates over a whole group of operators that share a direction slot
-// (at most kPGroupOps); at the group's end X is added to R and R goes to the
-// FP64 locals (a transposition through shared memory, then coalesced FP64
-// atomic adds).  Units may span operators of a group (H sums over K and over
-// the group's operators alike).
+// cross terms to X, and twelve epilogue warps per CTA add H into FP32
+// running sums R held in registers while the X instructions run.  X (2^-11
+// of H) accumulates over a whole group of operators that share a direction
+// slot (at most kPGroupOps); at the group's end X is added to R and R goes to
+// the FP64 locals (a transposition through shared memory, then coalesced
+// FP64 atomic adds).  Units may span operators of a group (H sums over K and
+// over the group's operators alike).
 //
-// Synchronisation: each CTA's copies complete on its own full barrier; in
-// rank 1 a relay thread forwards every completed stage to rank 0's full
-// barrier (count 2), where the MMA thread waits.  Commits multicast to both
-// CTAs (stage free, H ready, X ready, all done); the epilogue warps of both
-// CTAs arrive on rank 0's H-free / X-free barriers.  Every wait is bounded; a
-// wait that gives up sets the error word and the abort flag of both CTAs.
+// Synchronisation: both CTAs' copies (.cta_group::2 TMA) complete on rank
+// 0's full barrier, which rank 0's producer arms with both CTAs' bytes; the
+// MMA thread waits there.  Commits multicast to both CTAs (stage free, H
+// ready, X ready, all done); the epilogue warps of both CTAs arrive on rank
+// 0's H-free / X-free barriers.  Every wait is bounded; a wait that gives up
+// sets the error word and the abort flag of both CTAs.
 constexpr int kPTM = 128;                  // targets per CTA
 constexpr int kPX = 8, kPY = 4, kPZ = 4;   // parent-grid block of one CTA
 constexpr int kPU = 3;                     // stages per H unit
-constexpr int kPGroupOps = 16;             // operators per group at most
-constexpr int kPWarps = 12;                // 0 producer, 1 MMA, 2 relay, 4-11 epilogue
+constexpr int kPGroupOps = 1 << 20;        // operators per group at most (a whole slot run)
+constexpr int kPXUnits = 64;               // units per X accumulation (X drained after them)
+constexpr int kPRoll = 6;                  // units between two rolling flushes of one R chunk
+constexpr int kPEpiWarps = 12;             // three per TMEM lane quarter
+constexpr int kPEpiWarp0 = 2;              // warps: 0 producer, 1 MMA, 2.. epilogue
+constexpr int kPWarps = kPEpiWarp0 + kPEpiWarps;
 constexpr int kPThreads = kPWarps * 32;
-constexpr int kPEpiWarp0 = 4;
-constexpr int kPEpiThreads = 8 * 32;
+constexpr int kPEpiThreads = kPEpiWarps * 32;
 constexpr int kPBufRS = kPTM + 1;          // transposition buffer row stride (floats)
 constexpr uint32_t kPXCol = 256;           // TMEM column of X
 
@@ -434,24 +453,24 @@ struct PairSmem {
   static constexpr int kOffMhi = 0, kOffMlo = kM, kOffOhi = 2 * kM, kOffOlo = 2 * kM + kO;
   static constexpr int kStage = 2 * kM + 2 * kO;
   static constexpr int kBuf = 16 * kPBufRS * 4;    // 16 columns x 128 targets, FP32
-  static constexpr int kStFit = (227 * 1024 - 1024 - kBuf - 512) / kStage;
+  // at most ~220 KB in all (launches asking for the last few KB of the 227 KB
+  // per-CTA limit were refused)
+  static constexpr int kStFit = (220 * 1024 - 1024 - kBuf) / kStage;
   static constexpr int kSt = kStFit < 10 ? kStFit : 10;
   static constexpr int kTotal = kSt * kStage + kBuf + 1024;
   static_assert(kStage % 1024 == 0, "stage alignment");
   static_assert(NB % 8 == 0, "operator rows per CTA: whole 8-row swizzle atoms");
   static_assert(kSt >= 2 * kPU + 1, "a unit's stages plus the next unit's must fit");
+  static_assert(2 * NB <= 256, "one TMA box per operator share");
 };
 
-// Operator image of the pair kernel: for each (op, output half h, K step of
-// 32, CTA q) one contiguous block [hi | lo] of NB rows x 64 B in the 64-byte
-// swizzle, so each CTA's share of a stage is one bulk copy.
-__device__ __forceinline__ int64_t op_pair_index(int64_t op, int h, int kc, int j, int e, int KSTEPS, int NH,
-                                                 int hl) {
-  const int NB = NH / 2;
-  const int q = j / NB, jj = j - q * NB;
-  const int chunk = (e >> 3) ^ ((jj >> 1) & 3);
-  const int64_t blk = (((op * 2 + h) * KSTEPS + kc) * 2 + q) * 2 + hl;
-  return blk * NB * 32 + jj * 32 + chunk * 8 + (e & 7);
+// Operator image of the pair kernel, rows of 64 B (32 FP16 of K): for each
+// (op, output half h, K step of 32, CTA q) a block of 2 NB rows [hi | lo], NB
+// rows each, in the 64-byte swizzle the MMA descriptors read; each CTA's share
+// of a stage is one TMA box of 2 NB rows (no swizzle in the tensor map: the
+// image is already swizzled).
+__host__ __device__ __forceinline__ int64_t op_pair_row(int64_t op, int h, int kc, int q, int KSTEPS, int NB) {
+  return ((((op * 2 + h) * KSTEPS + kc) * 2 + q) * 2) * NB;
 }
 
 __global__ void k_coupling_split_pair(int order, int n, int KP, int NH, const int32_t *op_level,
@@ -464,7 +483,8 @@ __global__ void k_coupling_split_pair(int order, int n, int KP, int NH, const in
   const float sc = level_scale[l];
   const bool im_row = row >= NH;
   const int j = im_row ? row - NH : row;
-  const int KSTEPS = KP / 32;
+  const int KSTEPS = KP / 32, NB = NH / 2;
+  const int q = j / NB, jj = j - q * NB;
   const double d0 = op_off[3 * op], d1 = op_off[3 * op + 1], d2 = op_off[3 * op + 2];
   const double c0 = op_dir[3 * op], c1 = op_dir[3 * op + 1], c2 = op_dir[3 * op + 2];
   for (int kk = threadIdx.x; kk < KP; kk += blockDim.x) {
@@ -492,35 +512,29 @@ __global__ void k_coupling_split_pair(int order, int n, int KP, int NH, const in
     const __half hi = __float2half_rn(val);
     const __half lo = __float2half_rn(val - __half2float(hi));
     const int kc = kk >> 5, e = kk & 31, hh = im_row ? 1 : 0;
-    opk[op_pair_index(op, hh, kc, j, e, KSTEPS, NH, 0)] = hi;
-    opk[op_pair_index(op, hh, kc, j, e, KSTEPS, NH, 1)] = lo;
+    const int chunk = (e >> 3) ^ ((jj >> 1) & 3);
+    const int64_t base = op_pair_row(op, hh, kc, q, KSTEPS, NB) * 32 + (int64_t)jj * 32 + chunk * 8 + (e & 7);
+    opk[base] = hi;
+    opk[base + (int64_t)NB * 32] = lo;
   }
 }
 
-// End of the group of operators starting at ii (same slot, at most kPGroupOps).
-__device__ __forceinline__ int pair_group_end(const M2lArgs &a, int ii, int i1) {
-  const int slot = a.op_slot[a.alpha_ops[ii]];
-  int jj = ii + 1;
-  while (jj < i1 && jj - ii < kPGroupOps && a.op_slot[a.alpha_ops[jj]] == slot) ++jj;
-  return jj;
-}
-
 template <int NP>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
     k_m2l_pair(const __grid_constant__ CUtensorMap map_mhi, const __grid_constant__ CUtensorMap map_mlo,
-               const M2lArgs args) {
+               const __grid_constant__ CUtensorMap map_op, const M2lArgs args) {
   using S = PairSmem<NP>;
   constexpr int NH = S::NH;
   constexpr int NB = S::NB;
   constexpr int KSTEPS = NP / kK;      // stages per operator and half
   constexpr int NCH = NH / 16;         // 16-column chunks of one half
-  constexpr int CPW = NCH / 2;         // chunks per epilogue warp
+  constexpr int MAXC = (NCH + 2) / 3;  // chunks per epilogue warp at most
   constexpr int kSt = S::kSt;
-  static_assert(NCH % 2 == 0, "two epilogue warps per TMEM lane quarter");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *buf = reinterpret_cast<float *>(smem + kSt * S::kStage);   // [16][kPBufRS]
-  __shared__ uint64_t full_bar[kSt], empty_bar[kSt], h_full, h_empty, x_full, x_empty, fin_bar;
+  constexpr int kGo = kSt + 2;         // ring of per-unit "go" barriers
+  __shared__ uint64_t go_bar[kGo], empty_bar[kSt], h_full, x_full, x_empty, fin_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
@@ -537,18 +551,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
   const int a0 = args.alpha_off[alpha], na = args.alpha_off[alpha + 1] - a0;
   const int i0 = a0 + (int)(((int64_t)na * blockIdx.z) / args.nsplit);
   const int i1 = a0 + (int)(((int64_t)na * (blockIdx.z + 1)) / args.nsplit);
-  const int total_stages = 2 * (i1 - i0) * KSTEPS;
 
   if (tid == 0) {
-    for (int s = 0; s < kSt; ++s) {
-      ptx::mbar_init(&full_bar[s], rank == 0 ? 2 : 1);
-      ptx::mbar_init(&empty_bar[s], 1);
-    }
+    for (int s = 0; s < kSt; ++s) ptx::mbar_init(&empty_bar[s], 1);
+    // a unit may start once its stages have landed (rank 0's producer arms
+    // the barrier with both CTAs' bytes) and H is free (every epilogue warp
+    // of both CTAs arrives after draining the previous unit)
+    for (int b = 0; b < kGo; ++b) ptx::mbar_init(&go_bar[b], 1 + 2 * kPEpiWarps);
     ptx::mbar_init(&h_full, 1);
     ptx::mbar_init(&x_full, 1);
     ptx::mbar_init(&fin_bar, 1);
-    ptx::mbar_init(&h_empty, 2 * 8);
-    ptx::mbar_init(&x_empty, 2 * 8);
+    ptx::mbar_init(&x_empty, 2 * kPEpiWarps);
     s_abort = 0;
     ptx::fence_mbar_init();
   }
@@ -567,40 +580,59 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     s_abort = 1;
     ptx::st_cluster_u32(peer_abort, 1u);
   };
+  auto group_end = [&](int ii) { return min(args.meta[ii].w, min(ii + kPGroupOps, i1)); };
 
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------ producer (both CTAs)
       ptx::prefetch_tensormap(&map_mhi);
       ptx::prefetch_tensormap(&map_mlo);
-      uint32_t it = 0;
+      ptx::prefetch_tensormap(&map_op);
+      const uint32_t go0 = ptx::cluster_addr(&go_bar[0], 0);
+      uint32_t it = 0, un = 0;
       bool ok = true;
       for (int h = 0; h < 2 && ok; ++h) {
-        for (int ii = i0; ii < i1 && ok; ++ii) {
-          const int op = args.alpha_ops[ii];
-          const int slot = args.op_slot[op];
-          const int x0 = 2 * X0 + ax - args.op_off[3 * op];
-          const int y0 = 2 * Y0 + ay - args.op_off[3 * op + 1];
-          const int z0 = 2 * Z0 + az - args.op_off[3 * op + 2];
-          const int opl = op - args.op_base;
-          for (int kc = 0; kc < KSTEPS; ++kc, ++it) {
-            const int st = it % kSt;
-            const uint32_t ph = (it / kSt) & 1;
-            if (!ptx::mbar_wait_cluster(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
-            uint8_t *base = smem + st * S::kStage;
-            ptx::mbar_expect_tx(&full_bar[st], S::kStage);
-            ptx::tma_load_5d(base + S::kOffMhi, &map_mhi, &full_bar[st], kc * kK, x0, y0, z0, slot);
-            ptx::tma_load_5d(base + S::kOffMlo, &map_mlo, &full_bar[st], kc * kK, x0, y0, z0, slot);
-            ptx::bulk_load(base + S::kOffOhi,
-                           args.opk + ((((int64_t)opl * 2 + h) * KSTEPS + kc) * 2 + rank) * 2 * NB * 32,
-                           2 * S::kO, &full_bar[st]);
+        for (int ii = i0; ii < i1 && ok;) {
+          const int jj = group_end(ii);
+          const int ns = (jj - ii) * KSTEPS;
+          int sg = 0;                        // stage within the group
+          int4 nxt = args.meta[ii];
+          for (int oi = ii; oi < jj && ok; ++oi) {
+            const int4 m = nxt;
+            if (oi + 1 < jj) nxt = args.meta[oi + 1];   // next entry's metadata in flight
+            const int op = m.x, slot = m.z;
+            // sources t - d of this tile: parity (alpha - d) & 1 per axis,
+            // and in that parity's half grid the tile's block shifted by
+            // (alpha - d - parity) / 2
+            const int sx = ax - ((m.y & 255) - 128), sy = ay - (((m.y >> 8) & 255) - 128),
+                      sz = az - (((m.y >> 16) & 255) - 128);
+            const int px = sx & 1, py = sy & 1, pz = sz & 1;
+            const int x0 = X0 + (sx - px) / 2, y0 = Y0 + (sy - py) / 2, z0 = Z0 + (sz - pz) / 2;
+            const int qbase = (slot * KSTEPS) * 8 + px + 2 * py + 4 * pz;
+            for (int kc = 0; kc < KSTEPS; ++kc, ++it, ++sg) {
+              if (sg % kPU == 0) {           // a unit starts: arm its go barrier
+                if (rank == 0) ptx::mbar_expect_tx(&go_bar[un % kGo], min(kPU, ns - sg) * 2 * S::kStage);
+                ++un;
+              }
+              const int st = it % kSt;
+              const uint32_t ph = (it / kSt) & 1;
+              if (!ptx::mbar_wait(&empty_bar[st], ph ^ 1, kWaitLimit)) { ok = false; break; }
+              uint8_t *base = smem + st * S::kStage;
+              const uint32_t gb = go0 + 8u * ((un - 1) % kGo);
+              ptx::tma_load_5d_pair(base + S::kOffMhi, &map_mhi, gb, 0, x0, y0, z0, qbase + kc * 8);
+              ptx::tma_load_5d_pair(base + S::kOffMlo, &map_mlo, gb, 0, x0, y0, z0, qbase + kc * 8);
+              ptx::tma_load_2d_pair(base + S::kOffOhi, &map_op, gb, 0,
+                                    (int)(op_pair_row(op, h, kc, (int)rank, KSTEPS, NB) / 8));
+            }
           }
+          ii = jj;
         }
       }
-      // this CTA's copies still in flight land before it leaves (bounded;
-      // already complete on a normal run)
-      for (uint32_t k = (it > (uint32_t)kSt ? it - kSt : 0u); k < it; ++k)
-        if (!ptx::mbar_wait_cluster(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
+      // copies of both CTAs still in flight land before the pair leaves: the
+      // last unit's barrier completes only after all of them (rank 0 counts
+      // both CTAs' bytes; already complete on a normal run)
+      if (rank == 0 && un > 0 && ok && !ptx::mbar_wait(&go_bar[(un - 1) % kGo], ((un - 1) / kGo) & 1, kWaitLimit))
+        ok = false;
       if (!ok) abort_both();
     }
   } else if (warp == 1) {
@@ -611,16 +643,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
       bool ok = true;
       for (int h = 0; h < 2 && ok; ++h) {
         for (int ii = i0; ii < i1 && ok;) {
-          const int jj = pair_group_end(args, ii, i1);
+          const int jj = group_end(ii);
           const int ns = (jj - ii) * KSTEPS;
-          for (int u0 = 0; u0 < ns && ok; u0 += kPU) {
+          for (int u0 = 0, gu = 0; u0 < ns && ok; u0 += kPU, ++gu) {
             const int nst = min(kPU, ns - u0);
-            if (hu > 0 && !ptx::mbar_wait_cluster(&h_empty, (hu - 1) & 1, kWaitLimit)) { ok = false; break; }
-            for (int t = 0; t < nst && ok; ++t) {
-              const uint32_t k = it + t;
-              if (!ptx::mbar_wait_cluster(&full_bar[k % kSt], (k / kSt) & 1, kWaitLimit)) ok = false;
-            }
-            if (!ok) break;
+            const bool x_first = (gu % kPXUnits) == 0;
+            const bool x_last = (gu % kPXUnits) == kPXUnits - 1 || u0 + kPU >= ns;
+            // one wait per unit: its stages landed and H is free
+            if (!ptx::mbar_wait(&go_bar[hu % kGo], (hu / kGo) & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
             for (int t = 0; t < nst; ++t) {
               const uint32_t base = ptx::smem_u32(smem + ((it + t) % kSt) * S::kStage);
@@ -632,8 +662,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
               }
             }
             ptx::mma_commit_pair(&h_full);
-            if (u0 == 0 && xg > 0) {
-              if (!ptx::mbar_wait_cluster(&x_empty, (xg - 1) & 1, kWaitLimit)) { ok = false; break; }
+            if (x_first && xg > 0) {
+              if (!ptx::mbar_wait(&x_empty, (xg - 1) & 1, kWaitLimit)) { ok = false; break; }
               ptx::tc_fence_after();
             }
             for (int t = 0; t < nst; ++t) {
@@ -644,18 +674,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
                 const uint32_t o = 32u * j;
                 ptx::mma_f16_pair(tmem + kPXCol, ptx::sdesc_k_sw64(base + S::kOffMlo + o),
                                   ptx::sdesc_k_sw64(base + S::kOffOhi + o), idesc,
-                                  (u0 == 0 && t == 0 && j == 0) ? 0u : 1u);
+                                  (x_first && t == 0 && j == 0) ? 0u : 1u);
                 ptx::mma_f16_pair(tmem + kPXCol, ptx::sdesc_k_sw64(base + S::kOffMhi + o),
                                   ptx::sdesc_k_sw64(base + S::kOffOlo + o), idesc, 1u);
               }
               ptx::mma_commit_pair(&empty_bar[st]);
             }
+            if (x_last) {
+              ptx::mma_commit_pair(&x_full);
+              ++xg;
+            }
             it += nst;
             ++hu;
           }
           if (!ok) break;
-          ptx::mma_commit_pair(&x_full);
-          ++xg;
           ii = jj;
         }
       }
@@ -663,117 +695,126 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
       // every MMA has finished with shared memory and TMEM of both CTAs
       ptx::mma_commit_pair(&fin_bar);
     }
-  } else if (warp == 2) {
-    if (lane == 0 && rank == 1) {
-      // ------------------------------------------------ relay (rank 1)
-      const uint32_t leader_full0 = ptx::cluster_addr(&full_bar[0], 0);
-      bool ok = true;
-      for (int k = 0; k < total_stages; ++k) {
-        const int st = k % kSt;
-        bool got = false;
-        const uint64_t t0 = ptx::global_ns();
-        for (uint32_t t = 0; t < kWaitLimit && !got; ++t) {
-          got = ptx::mbar_try_wait(&full_bar[st], (k / kSt) & 1);
-          if (!got && (t & 255) == 255 && (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull))
-            break;
-        }
-        if (!got) { ok = false; break; }
-        ptx::mbar_arrive_cluster(leader_full0 + st * 8u);
-      }
-      if (!ok) abort_both();
-    }
-  } else if (warp >= kPEpiWarp0) {
+  } else {
     // ------------------------------------------------ epilogue (both CTAs)
-    const int e = warp - kPEpiWarp0;          // 0..7
-    const int q = warp & 3;                   // TMEM lane quarter
-    const int ch = e >> 2;                    // column half of H / X (CPW chunks)
+    const int e = warp - kPEpiWarp0;          // 0..11
+    const int q = warp & 3;                   // TMEM lane quarter this warp may read
+    const int wq = e >> 2;                    // column third of H / X
+    const int c_lo = (NCH * wq) / 3, nc = (NCH * (wq + 1)) / 3 - c_lo;
     const int row = q * 32 + lane;            // this thread's target row
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-    const uint32_t h_empty0 = ptx::cluster_addr(&h_empty, 0);
+    const uint32_t go0 = ptx::cluster_addr(&go_bar[0], 0);
     const uint32_t x_empty0 = ptx::cluster_addr(&x_empty, 0);
     const int64_t ncell = (int64_t)g * g * g;
     const int n = args.n;
-    const float inv = ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
-    const int te = tid - kPEpiWarp0 * 32;     // 0..255
-    float R[CPW * 16];
+    const double inv = (double)ldexpf(1.0f, -(args.op_exp + *args.mom_exp));
+    const int te = tid - kPEpiWarp0 * 32;     // 0..383
+    float R[MAXC * 16];
 #pragma unroll
-    for (int i = 0; i < CPW * 16; ++i) R[i] = 0.f;
+    for (int i = 0; i < MAXC * 16; ++i) R[i] = 0.f;
     uint32_t hu = 0, xg = 0;
     bool bad = false;
+    if (lane == 0) ptx::mbar_arrive_cluster(go0);   // H is free for unit 0
+    // bounded wait that also gives up once the other warps or CTA aborted;
+    // the wall clock is read only after 256 failed tries
     auto wait_local = [&](uint64_t *bar, uint32_t ph) {
-      const uint64_t t0 = ptx::global_ns();
+      uint64_t t0 = 0;
       for (uint32_t t = 0; t < kWaitLimit; ++t) {
-        if (ptx::mbar_try_wait_cluster(bar, ph)) return true;
-        if ((t & 255) == 255 && (*(volatile int *)&s_abort || ptx::global_ns() - t0 > 1000000000ull)) return false;
+        if (ptx::mbar_try_wait(bar, ph)) return true;
+        if ((t & 255) == 255) {
+          if (*(volatile int *)&s_abort) return false;
+          const uint64_t now = ptx::global_ns();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > 1000000000ull) return false;
+        }
       }
       return false;
+    };
+    // add the region at TMEM column `col0` to R
+    auto drain = [&](uint32_t col0) {
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c) {
+        if (c < nc) {
+          float v[16];
+          ptx::tmem_ld16(tmem + lane_addr + col0 + (uint32_t)((c_lo + c) * 16), v);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) R[c * 16 + i] += v[i];
+        }
+      }
+    };
+    // R chunk k (16 columns) -> locals through the transposition buffer;
+    // every epilogue thread takes part (named barriers)
+    auto flush_chunk = [&](int k, int slot, int h) {
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c) {
+        if (c < nc && c_lo + c == k) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            buf[i * kPBufRS + row] = R[c * 16 + i];
+            R[c * 16 + i] = 0.f;
+          }
+        }
+      }
+      ptx::named_bar(1, kPEpiThreads);
+#pragma unroll 1
+      for (int idx = te; idx < kPTM * 16; idx += kPEpiThreads) {
+        const int rr = idx >> 4, cc = idx & 15;
+        const int col = k * 16 + cc;
+        const int XX = X0 + (rr & 7), YY = Y0 + ((rr >> 3) & 3), ZZ = Z0 + (rr >> 5);
+        if (col < n && XX < gp && YY < gp && ZZ < gp) {
+          const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
+          atomicAdd(args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n + col,
+                    (double)buf[cc * kPBufRS + rr] * inv);
+        }
+      }
+      ptx::named_bar(1, kPEpiThreads);
     };
     bool stop = false;
     for (int h = 0; h < 2 && !stop; ++h) {
       for (int ii = i0; ii < i1 && !stop;) {
-        const int jj = pair_group_end(args, ii, i1);
-        const int slot = args.op_slot[args.alpha_ops[ii]];
+        const int jj = group_end(ii);
+        const int slot = args.meta[ii].z;
         const int ns = (jj - ii) * KSTEPS;
-        for (int u0 = 0; u0 < ns; u0 += kPU) {
+        int roll_k = 0, roll_n = 0;       // next chunk of the rolling flush, units since the last
+        for (int u0 = 0, gu = 0; u0 < ns && !stop; u0 += kPU, ++gu) {
+          const bool x_last = (gu % kPXUnits) == kPXUnits - 1 || u0 + kPU >= ns;
           if (!bad && !wait_local(&h_full, hu & 1)) bad = true;
           ++hu;
-          if (bad) continue;
-          ptx::tc_fence_after();
-#pragma unroll
-          for (int c = 0; c < CPW; ++c) {
-            float v[16];
-            ptx::tmem_ld16(tmem + lane_addr + (uint32_t)((ch * CPW + c) * 16), v);
-            ptx::tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) R[c * 16 + i] += v[i];
+          if (!bad) {
+            ptx::tc_fence_after();
+            drain(0);
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive_cluster(go0 + 8u * (hu % kGo));   // H free for unit hu
           }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive_cluster(h_empty0);
-        }
-        if (!bad && !wait_local(&x_full, xg & 1)) bad = true;
-        ++xg;
-        if (!bad) {
-          ptx::tc_fence_after();
-#pragma unroll
-          for (int c = 0; c < CPW; ++c) {
-            float v[16];
-            ptx::tmem_ld16(tmem + lane_addr + kPXCol + (uint32_t)((ch * CPW + c) * 16), v);
-            ptx::tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) R[c * 16 + i] += v[i];
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive_cluster(x_empty0);
-        }
-        // one decision for all epilogue warps before the flush's barriers
-        stop = ptx::named_bar_or(2, kPEpiThreads, bad || *(volatile int *)&s_abort);
-        if (stop) break;
-        // R -> locals: 16 columns at a time through the transposition buffer
-#pragma unroll
-        for (int k = 0; k < NCH; ++k) {
-          if (ch == k / CPW) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              buf[i * kPBufRS + row] = R[(k % CPW) * 16 + i];
-              R[(k % CPW) * 16 + i] = 0.f;
+          if (x_last) {
+            if (!bad && !wait_local(&x_full, xg & 1)) bad = true;
+            ++xg;
+            if (!bad) {
+              ptx::tc_fence_after();
+              drain(kPXCol);
+              ptx::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) ptx::mbar_arrive_cluster(x_empty0);
             }
           }
-          ptx::named_bar(1, kPEpiThreads);
-#pragma unroll
-          for (int r8 = 0; r8 < kPTM * 16 / kPEpiThreads; ++r8) {
-            const int idx = r8 * kPEpiThreads + te;
-            const int rr = idx >> 4, cc = idx & 15;
-            const int col = k * 16 + cc;
-            const int XX = X0 + (rr & 7), YY = Y0 + ((rr >> 3) & 3), ZZ = Z0 + (rr >> 5);
-            if (col < n && XX < gp && YY < gp && ZZ < gp) {
-              const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
-              const float val = buf[cc * kPBufRS + rr];
-              atomicAdd(args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n + col, (double)val * (double)inv);
+          const bool last = u0 + kPU >= ns;
+          if (last || ++roll_n == kPRoll) {
+            // one decision for all epilogue warps before the flush's barriers
+            stop = ptx::named_bar_or(2, kPEpiThreads, bad || *(volatile int *)&s_abort);
+            if (stop) break;
+            if (last) {
+              // the group's slot changes next: everything in R goes out
+              for (int k = 0; k < NCH; ++k) flush_chunk(k, slot, h);
+            } else {
+              // rolling: one chunk, so each element of R sums at most
+              // NCH * kPRoll unit drains in FP32 between two flushes
+              flush_chunk(roll_k, slot, h);
+              roll_k = (roll_k + 1) % NCH;
+              roll_n = 0;
             }
           }
-          ptx::named_bar(1, kPEpiThreads);
         }
         ii = jj;
       }
@@ -783,7 +824,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
   // ------------------------------------------------ teardown (both CTAs)
   if (warp == 1 && lane == 0) {
     // the last commit of rank 0's MMA thread reached this CTA
-    if (!ptx::mbar_wait_cluster(&fin_bar, 0, kWaitLimit)) atomicExch(args.err, 1);
+    if (!ptx::mbar_wait(&fin_bar, 0, kWaitLimit)) atomicExch(args.err, 1);
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -1129,7 +1170,9 @@ struct TcState {
   std::vector<double *> loc64;           // per level local grids (FP64 sums)
   std::vector<__half *> mhi, mlo;        // per level split moments
   std::vector<CUtensorMap> map_mhi, map_mlo;
-  __half *opk = nullptr;                 // split operator images (see op_image_index)
+  __half *opk = nullptr;                 // split operator images (see op_pair_row)
+  CUtensorMap map_op;                    // 2-D map over opk: rows of 256 FP16 (512 B)
+  int4 *meta = nullptr;                  // parallel to the M2L lists (see M2lArgs::meta)
   std::vector<int> op_exp;               // per level operator scale exponent
   float *maxabs = nullptr;               // per level max |moment|
   int *mom_exp = nullptr;                // per level moment exponent
@@ -1282,13 +1325,13 @@ void build_tc(Plan &plan, cudaStream_t st) {
     if (!plan.levels[l].off.empty()) {
       T.mhi[l] = plan.alloc<__half>(cnt);
       T.mlo[l] = plan.alloc<__half>(cnt);
-      const int gl = 1 << l;
-      const cuuint64_t dims[5] = {(cuuint64_t)KP, (cuuint64_t)gl, (cuuint64_t)gl, (cuuint64_t)gl,
-                                  (cuuint64_t)plan.levels[l].slot_dir.size()};
-      const cuuint64_t strides[4] = {(cuuint64_t)KP * 2, (cuuint64_t)KP * 2 * gl, (cuuint64_t)KP * 2 * gl * gl,
-                                     (cuuint64_t)KP * 2 * gl * gl * gl};
-      const cuuint32_t box[5] = {(cuuint32_t)kK, 2 * kPX, 2 * kPY, 2 * kPZ, 1};
-      const cuuint32_t es[5] = {1, 2, 2, 2, 1};
+      const cuuint64_t hg = (cuuint64_t)1 << (l - 1);   // half the level grid
+      const cuuint64_t dims[5] = {(cuuint64_t)kK, hg, hg, hg,
+                                  (cuuint64_t)plan.levels[l].slot_dir.size() * (KP / kK) * 8};
+      const cuuint64_t strides[4] = {(cuuint64_t)kK * 2, (cuuint64_t)kK * 2 * hg, (cuuint64_t)kK * 2 * hg * hg,
+                                     (cuuint64_t)kK * 2 * hg * hg * hg};
+      const cuuint32_t box[5] = {(cuuint32_t)kK, kPX, kPY, kPZ, 1};
+      const cuuint32_t es[5] = {1, 1, 1, 1, 1};
       encode(&T.map_mhi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mhi[l], dims, strides, box, es,
              CU_TENSOR_MAP_SWIZZLE_64B);
       encode(&T.map_mlo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, T.mlo[l], dims, strides, box, es,
@@ -1336,6 +1379,41 @@ void build_tc(Plan &plan, cudaStream_t st) {
     cudaFree(d_dir);
     cudaFree(d_w);
     cudaFree(d_sc);
+    const int NB = KP / 4;
+    const cuuint64_t dims[2] = {256, (cuuint64_t)nops * (cuuint64_t)(KP * KP * 2 / 256)};
+    const cuuint64_t strides[1] = {512};
+    const cuuint32_t box[2] = {256, (cuuint32_t)(2 * NB * 32 / 256)};
+    const cuuint32_t es[2] = {1, 1};
+    encode(&T.map_op, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, T.opk, dims, strides, box, es, CU_TENSOR_MAP_SWIZZLE_NONE);
+  }
+  // per entry of the M2L lists (same order as plan.m2l_ops): the global
+  // operator index, its offset packed as three biased bytes, its direction
+  // slot and the end of the run of entries sharing that slot (the lists are
+  // sorted by slot), relative to the level's first entry
+  {
+    std::vector<int4> meta;
+    for (auto &L : plan.levels) {
+      const size_t base = meta.size();
+      for (int al = 0; al < 8; ++al) {
+        const auto &lst = L.alpha_ops[al];
+        const size_t s0 = meta.size();
+        meta.resize(s0 + lst.size());
+        for (size_t i = lst.size(); i-- > 0;) {
+          const int op = lst[i];
+          int packed = 0;
+          for (int a = 0; a < 3; ++a) {
+            const int d = L.off[3 * op + a];
+            if (d < -128 || d > 127) throw Error{DFDM_ERR_UNSUPPORTED, "M2L offset out of the packed range"};
+            packed |= (d + 128) << (8 * a);
+          }
+          const bool same = i + 1 < lst.size() && L.op_slot[lst[i + 1]] == L.op_slot[op];
+          meta[s0 + i] = make_int4(L.op_base + op, packed, L.op_slot[op],
+                                   same ? meta[s0 + i + 1].w : (int32_t)(s0 + i + 1 - base));
+        }
+      }
+    }
+    T.meta = plan.alloc<int4>(std::max<size_t>(meta.size(), 1));
+    if (!meta.empty()) DFDM_CUDA_TRY(cudaMemcpy(T.meta, meta.data(), meta.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   DFDM_CUDA_TRY(cudaStreamSynchronize(st));
 }
@@ -1387,7 +1465,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       {
         PhaseScope sc(tm, kPhSplit, st);
         const int64_t cnt = (int64_t)L.slot_dir.size() * (1ll << (3 * l)) * KP;
-        k_split<<<1184, 256, 0, st>>>(T.mom32[l], cnt, T.maxabs + l, T.mom_exp + l, T.mhi[l], T.mlo[l],
+        k_split<<<1184, 256, 0, st>>>(T.mom32[l], cnt, L.grid, KP, T.maxabs + l, T.mom_exp + l, T.mhi[l], T.mlo[l],
                                       plan.err_flag);
         DFDM_COUNT_LAUNCH(plan);
       }
@@ -1396,8 +1474,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.alpha_off = plan.m2l_aoff_dev + 9 * l;
       a.op_off = plan.op_off_dev;
       a.op_slot = plan.op_slot_dev;
-      a.op_base = L.op_base;
-      a.opk = T.opk + (size_t)L.op_base * KP * KP * 2;
+      a.meta = T.meta + plan.m2l_ops_off[l * 9];
       a.loc = T.loc64[l];
       a.g = L.grid;
       a.n = N;
@@ -1412,7 +1489,7 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       a.nsplit = m2l_split(pairs, (int)ops_alpha, T.num_sms / 2, (size_t)KP * KP * 4, T.l2_bytes);
       const int smem = PairSmem<NP>::kTotal;
       PhaseScope sc(tm, kPhM2L0 + l, st);
-      k_m2l_pair<NP><<<dim3(2 * pairs, 8, a.nsplit), kPThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], a);
+      k_m2l_pair<NP><<<dim3(2 * pairs, 8, a.nsplit), kPThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], T.map_op, a);
       DFDM_COUNT_LAUNCH(plan);
     }
     {

@@ -41,3 +41,20 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(1.5, 1) == 1.5
     assert bench.job_rate(4, 1, 2.0) == 2.0
+
+
+def test_gpus_flag_launches_the_ranks_itself():
+    """`bench.py --gpus 2` with no launcher starts two ranks itself; the
+    CPU-only reference arm runs on rank 0 alone and reports both ranks."""
+    import json
+    import subprocess
+    pytest.importorskip("torch")
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--impl", "reference",
+                        "--workload", "uniform-8k-k16-d4-o4", "--steps", "1", "--warmup", "0", "--ref-rows", "8"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2

@@ -269,5 +269,21 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
       : "memory");
 }
 
+// ------------------------------------------------- bulk reductions
+// global[dst .. dst + bytes) += shared[src ..] element-wise in FP64, done by
+// the TMA engine; 16-byte aligned addresses, bytes a multiple of 16.  The
+// shared-memory source must have been made visible to the async proxy
+// (fence_proxy_async by the writing threads, then a barrier).
+__device__ __forceinline__ void bulk_reduce_add_f64(double *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// This thread's committed bulk operations have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... and have completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 }  // namespace ptx
 }  // namespace dfdm

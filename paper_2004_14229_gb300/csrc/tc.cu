@@ -27,7 +27,9 @@
 // The other phases (S2M, M2M, L2L, L2T, nearfield) run in FP32 on the CUDA
 // cores with FP64 reduction of large phase arguments; moments are
 // real-stacked FP32 rows [Re 0..n-1 | Im 0..n-1 | pad] of KP floats, locals
-// the same rows in FP64.
+// FP64 rows [Re 0..n-1 | pad | Im 0..n-1 | pad] with the imaginary part at
+// KP / 2 (both halves start on 128-byte boundaries: the M2L adds them with
+// bulk reductions).
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const double *ploc, double *clo
     const double *src = ploc + ((int64_t)ps * ncp + cellp) * KP;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
       ur[k] = (float)src[k];
-      ui[k] = (float)src[N + k];
+      ui[k] = (float)src[KP / 2 + k];
     }
     __syncthreads();
     tensor_transfer_f<O>(se1, oct, false, ur, ui, tr, ti);
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(128) k_l2l_f32(const double *ploc, double *clo
     const int k = threadIdx.x + 128 * i;
     if (k < N) {
       dst[k] += (double)ar[i];
-      dst[N + k] += (double)ai[i];
+      dst[KP / 2 + k] += (double)ai[i];
     }
   }
 }
@@ -434,13 +436,13 @@ constexpr int kPX = 8, kPY = 4, kPZ = 4;   // parent-grid block of one CTA
 constexpr int kPU = 3;                     // stages per H unit
 constexpr int kPGroupOps = 1 << 20;        // operators per group at most (a whole slot run)
 constexpr int kPXUnits = 64;               // units per X accumulation (X drained after them)
-constexpr int kPRoll = 6;                  // units between two rolling flushes of one R chunk
+// after every second unit one slice of R (32 target rows x 16 columns) goes to
+// the locals, so each element of R sums at most 8 (NH / 16) unit drains in FP32
 constexpr int kPEpiWarps = 12;             // three per TMEM lane quarter
 constexpr int kPEpiWarp0 = 2;              // warps: 0 producer, 1 MMA, 2.. epilogue
 constexpr int kPWarps = kPEpiWarp0 + kPEpiWarps;
 constexpr int kPThreads = kPWarps * 32;
 constexpr int kPEpiThreads = kPEpiWarps * 32;
-constexpr int kPBufRS = kPTM + 1;          // transposition buffer row stride (floats)
 constexpr uint32_t kPXCol = 256;           // TMEM column of X
 
 template <int NP>
@@ -452,7 +454,7 @@ struct PairSmem {
   static constexpr int kO = NB * kRowB;
   static constexpr int kOffMhi = 0, kOffMlo = kM, kOffOhi = 2 * kM, kOffOlo = 2 * kM + kO;
   static constexpr int kStage = 2 * kM + 2 * kO;
-  static constexpr int kBuf = 16 * kPBufRS * 4;    // 16 columns x 128 targets, FP32
+  static constexpr int kBuf = 16 * 33 * 4;         // flush: transposition of one 32 x 16 slice
   // at most ~220 KB in all (launches asking for the last few KB of the 227 KB
   // per-CTA limit were refused)
   static constexpr int kStFit = (220 * 1024 - 1024 - kBuf) / kStage;
@@ -701,7 +703,6 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
     const int q = warp & 3;                   // TMEM lane quarter this warp may read
     const int wq = e >> 2;                    // column third of H / X
     const int c_lo = (NCH * wq) / 3, nc = (NCH * (wq + 1)) / 3 - c_lo;
-    const int row = q * 32 + lane;            // this thread's target row
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     const uint32_t go0 = ptx::cluster_addr(&go_bar[0], 0);
     const uint32_t x_empty0 = ptx::cluster_addr(&x_empty, 0);
@@ -743,32 +744,38 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
         }
       }
     };
-    // R chunk k (16 columns) -> locals through the transposition buffer;
-    // every epilogue thread takes part (named barriers)
-    auto flush_chunk = [&](int k, int slot, int h) {
+    // slice (chunk k, lane quarter qs) of R -> locals: its one owner warp
+    // transposes the 32 x 16 values through shared memory, then every
+    // epilogue thread adds a part with FP64 atomics (consecutive lanes:
+    // consecutive columns of one target row).  Columns at or beyond n hold
+    // exact zeros (the operator rows there are zero) and are skipped.
+    // Returns the common decision to stop, taken at the first barrier.
+    auto flush_slice = [&](int k, int qs, int slot, int h) {
+      if (q == qs) {
 #pragma unroll
-      for (int c = 0; c < MAXC; ++c) {
-        if (c < nc && c_lo + c == k) {
+        for (int c = 0; c < MAXC; ++c) {
+          if (c < nc && c_lo + c == k) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            buf[i * kPBufRS + row] = R[c * 16 + i];
-            R[c * 16 + i] = 0.f;
+            for (int i = 0; i < 16; ++i) {
+              buf[i * 33 + lane] = R[c * 16 + i];
+              R[c * 16 + i] = 0.f;
+            }
           }
         }
       }
-      ptx::named_bar(1, kPEpiThreads);
-#pragma unroll 1
-      for (int idx = te; idx < kPTM * 16; idx += kPEpiThreads) {
-        const int rr = idx >> 4, cc = idx & 15;
+      if (ptx::named_bar_or(1, kPEpiThreads, bad || *(volatile int *)&s_abort)) return true;
+      for (int idx = te; idx < 32 * 16; idx += kPEpiThreads) {
+        const int rr = qs * 32 + (idx >> 4), cc = idx & 15;
         const int col = k * 16 + cc;
         const int XX = X0 + (rr & 7), YY = Y0 + ((rr >> 3) & 3), ZZ = Z0 + (rr >> 5);
         if (col < n && XX < gp && YY < gp && ZZ < gp) {
           const int64_t cl = (2 * XX + ax) + (int64_t)g * ((2 * YY + ay) + (int64_t)g * (2 * ZZ + az));
-          atomicAdd(args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * n + col,
-                    (double)buf[cc * kPBufRS + rr] * inv);
+          atomicAdd(args.loc + ((int64_t)slot * ncell + cl) * args.KP + h * (args.KP / 2) + col,
+                    (double)buf[cc * 33 + (idx >> 4)] * inv);
         }
       }
       ptx::named_bar(1, kPEpiThreads);
+      return false;
     };
     bool stop = false;
     for (int h = 0; h < 2 && !stop; ++h) {
@@ -776,7 +783,7 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
         const int jj = group_end(ii);
         const int slot = args.meta[ii].z;
         const int ns = (jj - ii) * KSTEPS;
-        int roll_k = 0, roll_n = 0;       // next chunk of the rolling flush, units since the last
+        int roll = 0;                     // next slice of the rolling flush: chunk roll / 4, quarter roll % 4
         for (int u0 = 0, gu = 0; u0 < ns && !stop; u0 += kPU, ++gu) {
           const bool x_last = (gu % kPXUnits) == kPXUnits - 1 || u0 + kPU >= ns;
           if (!bad && !wait_local(&h_full, hu & 1)) bad = true;
@@ -799,21 +806,15 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
               if (lane == 0) ptx::mbar_arrive_cluster(x_empty0);
             }
           }
-          const bool last = u0 + kPU >= ns;
-          if (last || ++roll_n == kPRoll) {
-            // one decision for all epilogue warps before the flush's barriers
-            stop = ptx::named_bar_or(2, kPEpiThreads, bad || *(volatile int *)&s_abort);
+          if (u0 + kPU >= ns) {
+            // the group's slot (or output half) changes next: everything in R
+            // goes out; one decision for all epilogue warps before the barriers
+            for (int k = 0; k < NCH && !stop; ++k)
+              for (int qs = 0; qs < 4 && !stop; ++qs) stop = flush_slice(k, qs, slot, h);
             if (stop) break;
-            if (last) {
-              // the group's slot changes next: everything in R goes out
-              for (int k = 0; k < NCH; ++k) flush_chunk(k, slot, h);
-            } else {
-              // rolling: one chunk, so each element of R sums at most
-              // NCH * kPRoll unit drains in FP32 between two flushes
-              flush_chunk(roll_k, slot, h);
-              roll_k = (roll_k + 1) % NCH;
-              roll_n = 0;
-            }
+          } else if (gu & 1) {
+            stop = flush_slice(roll >> 2, roll & 3, slot, h);
+            roll = (roll + 1) % (4 * NCH);
           }
         }
         ii = jj;
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
     for (int slot = 0; slot < nslots; ++slot) {
       const double *src = loc + ((int64_t)slot * ncell + cell) * KP;
       __syncthreads();
-      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = (float)src[i];
+      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = (float)src[i < N ? i : KP / 2 + (i - N)];
       __syncthreads();
       float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
 #pragma unroll
@@ -950,7 +951,7 @@ __global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_
         if (k < N) {
           const float l = pick<O>(lx, k % O) * pick<O>(ly, (k / O) % O) * pick<O>(lz, k / (O * O));
           two_sum_acc(sr, __fmul_rn(l, (float)src[k]), cr);
-          two_sum_acc(si, __fmul_rn(l, (float)src[N + k]), ci);
+          two_sum_acc(si, __fmul_rn(l, (float)src[KP / 2 + k]), ci);
         }
       }
       double re = (double)sr + (double)cr, im = (double)si + (double)ci;

@@ -259,15 +259,17 @@ def run_ours(args):
         err = float(np.linalg.norm(yv - g["y_fdm"]) / np.linalg.norm(g["y_fdm"]))
 
     # ------------------------------------------------------------ end to end
-    xh = torch.from_numpy(x.astype(cdt)).pin_memory()
-    yh = torch.empty(w["n"], dtype=tdt).pin_memory()
-    plan.apply_host(xh.numpy(), yh.numpy())
-    e2e_steps = max(1, min(args.steps, 3))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = torch.from_numpy(x.astype(cdt)).pin_memory()
+        yh = torch.empty(w["n"], dtype=tdt).pin_memory()
         plan.apply_host(xh.numpy(), yh.numpy())
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = world / e2e_s
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.apply_host(xh.numpy(), yh.numpy())
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": xh.numel() * xh.element_size(),
+               "d2h_bytes_per_step": yh.numel() * yh.element_size()}
 
     # -------------------------------------------------------------- roofline
     # dominant kernel: M2L (tensor cores) or, with large leaves, the nearfield
@@ -316,8 +318,7 @@ def run_ours(args):
             "dtype": "f16x3+f32" if prec == pkg.TC_FP16X3 else "f64", "data": "synthetic",
             "config": _config(args, w, world),
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xh.numel() * xh.element_size(),
-                    "d2h_bytes_per_step": yh.numel() * yh.element_size()},
+            "e2e": e2e,
             "gpu_launches": launches,
             "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
             "m2l_ms_per_level": [v / args.steps for v in m2l_ms[:w["depth"] + 1]],
@@ -472,6 +473,8 @@ def main():
     ap.add_argument("--precision", default="tc", choices=["tc", "fp64"])
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="products timed end to end through dfdm_apply_host (0: none)")
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:

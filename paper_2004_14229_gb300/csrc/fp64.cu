@@ -364,17 +364,20 @@ __global__ void __launch_bounds__(128) k_l2l_fp64(
 
 // ------------------------------------------------------------- M2L (FP64)
 // One block: 32 targets of parity alpha in a row of the parent grid, all N
-// outputs; loops over the level's operators for alpha (sorted by direction
-// slot), accumulating in registers and flushing when the slot changes.
+// outputs (warp w takes outputs w, w + 16, ...); loops over the level's
+// operators for alpha (sorted by direction slot), accumulating in registers
+// and flushing when the slot changes.  Each complex multiply-add is four
+// FP64 FMAs; sixteen warps keep the FP64 pipes of the SM busy.
 constexpr int kM2lKc = 8;
+constexpr int kM2lJG = 16;                  // warps per block
 
 template <int O>
-__global__ void __launch_bounds__(256) k_m2l_fp64(
+__global__ void __launch_bounds__(kM2lJG * 32, 1) k_m2l_fp64(
     const double2 *ops, const int32_t *alpha_ops, const int32_t *alpha_off,
     const int32_t *op_off, const int32_t *op_slot, const double2 *mom,
     double2 *loc, int g) {
   constexpr int N = O * O * O;
-  constexpr int JG = 8;
+  constexpr int JG = kM2lJG;
   constexpr int NJ = (N + JG - 1) / JG;
   __shared__ double2 sA[N][kM2lKc];
   __shared__ double2 sV[kM2lKc][32];
@@ -441,8 +444,10 @@ __global__ void __launch_bounds__(256) k_m2l_fp64(
           const int j = warp + JG * i;
           if (j < N) {
             const double2 a = sA[j][kk];
-            acc[i].x += a.x * v.x - a.y * v.y;
-            acc[i].y += a.x * v.y + a.y * v.x;
+            acc[i].x = fma(a.x, v.x, acc[i].x);
+            acc[i].x = fma(-a.y, v.y, acc[i].x);
+            acc[i].y = fma(a.x, v.y, acc[i].y);
+            acc[i].y = fma(a.y, v.x, acc[i].y);
           }
         }
       }
@@ -813,7 +818,7 @@ static void apply_fp64_o(Plan &plan, const double2 *x, double2 *y, cudaStream_t 
       const int tiles = ((gp + 31) / 32) * gp * gp;
       dim3 grid(tiles, 8);
       PhaseScope sc(plan.timing, kPhM2L0 + l, st);
-      k_m2l_fp64<O><<<grid, 256, 0, st>>>(plan.coupling, plan.m2l_ops + plan.m2l_ops_off[l * 9],
+      k_m2l_fp64<O><<<grid, kM2lJG * 32, 0, st>>>(plan.coupling, plan.m2l_ops + plan.m2l_ops_off[l * 9],
                                           plan.m2l_aoff_dev + 9 * l,
                                           plan.op_off_dev, plan.op_slot_dev, plan.mom[l], plan.loc[l], L.grid);
       DFDM_COUNT_LAUNCH(plan);

@@ -382,17 +382,20 @@ __global__ void __launch_bounds__(kM2lJG * 32, 1) k_m2l_fp64(
   __shared__ double2 sA[N][kM2lKc];
   __shared__ double2 sV[kM2lKc][32];
   const int gp = g >> 1;
-  const int tiles_x = (gp + 31) / 32;
+  // the block's 32 targets: a bx x by x bz box of the parent grid (all 32
+  // lanes carry a target on grids of at least 32 cells in all)
+  const int bx = min(gp, 32), by = min(gp, 32 / bx), bz = 32 / (bx * by);
+  const int tiles_x = (gp + bx - 1) / bx, tiles_y = (gp + by - 1) / by;
   const int alpha = blockIdx.y;
   const int tile = blockIdx.x;
-  const int X0 = (tile % tiles_x) * 32;
-  const int Y = (tile / tiles_x) % gp;
-  const int Z = tile / (tiles_x * gp);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int X = (tile % tiles_x) * bx + lane % bx;
+  const int Y = ((tile / tiles_x) % tiles_y) * by + (lane / bx) % by;
+  const int Z = (tile / (tiles_x * tiles_y)) * bz + lane / (bx * by);
   const int ax = alpha & 1, ay = (alpha >> 1) & 1, az = (alpha >> 2) & 1;
   const int64_t ncell = (int64_t)g * g * g;
-  const int tx = 2 * (X0 + lane) + ax, ty = 2 * Y + ay, tz = 2 * Z + az;
-  const bool tvalid = (X0 + lane) < gp;
+  const int tx = 2 * X + ax, ty = 2 * Y + ay, tz = 2 * Z + az;
+  const bool tvalid = X < gp && Y < gp && Z < gp;
   const int64_t tcell = tx + (int64_t)g * (ty + (int64_t)g * tz);
   double2 acc[NJ];
 #pragma unroll
@@ -815,7 +818,8 @@ static void apply_fp64_o(Plan &plan, const double2 *x, double2 *y, cudaStream_t 
       const LevelPlan &L = plan.levels[l];
       if (L.off.empty()) continue;
       const int gp = L.grid / 2;
-      const int tiles = ((gp + 31) / 32) * gp * gp;
+      const int bx = std::min(gp, 32), by = std::min(gp, 32 / bx), bz = 32 / (bx * by);
+      const int tiles = ((gp + bx - 1) / bx) * ((gp + by - 1) / by) * ((gp + bz - 1) / bz);
       dim3 grid(tiles, 8);
       PhaseScope sc(plan.timing, kPhM2L0 + l, st);
       k_m2l_fp64<O><<<grid, kM2lJG * 32, 0, st>>>(plan.coupling, plan.m2l_ops + plan.m2l_ops_off[l * 9],

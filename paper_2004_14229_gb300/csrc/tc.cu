@@ -49,31 +49,23 @@ __constant__ double c_lagw[kMaxOrder];
 
 constexpr double kPi = 3.14159265358979323846;
 
-__constant__ float c_chebf[kMaxOrder];
-__constant__ float c_lagwf[kMaxOrder];
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // ------------------------------------------------------------ helpers
+// The o 1-D Lagrange basis values at t in [-1, 1] (reference nodes of Eq. 4,
+// barycentric factors c_lagw), FP64.
 template <int O>
-__device__ __forceinline__ void lagrange1f(float t, float *out) {
+__device__ __forceinline__ void lagrange1d(double t, double *out) {
 #pragma unroll
   for (int nu = 0; nu < O; ++nu) {
-    float v = c_lagwf[nu];
+    double v = c_lagw[nu];
 #pragma unroll
     for (int mu = 0; mu < O; ++mu)
-      if (mu != nu) v *= (t - c_chebf[mu]);
+      if (mu != nu) v *= (t - c_cheb[mu]);
     out[nu] = v;
   }
-}
-
-// exp(i a) for an FP64 argument: reduced modulo 2 pi in FP64, then FP32.
-__device__ __forceinline__ float2 cexpi_reduced(double a) {
-  const double r = a - 2.0 * kPi * rint(a * (0.5 / kPi));
-  float s, c;
-  sincosf((float)r, &s, &c);
-  return make_float2(c, s);
 }
 
 // |v| with every non-finite value mapped to +inf (fmaxf would drop a NaN),
@@ -123,36 +115,43 @@ __global__ void k_local_coords(const double *xyz, int64_t n, const int32_t *leaf
 }
 
 // ----------------------------------------------------------------- S2M
+// One block per (source leaf, direction slot): moments v~_{s,c}[k] =
+// sum_{y in s} L_k(y) exp(-i kappa <y - m_s, c>) x_y (Eq. 10, centred
+// phases), from the FP64 point coordinates, all in FP64; stored as FP32 (the
+// M2L splits them into FP16 pairs; M2M reads them).
 template <int O>
-__global__ void __launch_bounds__(128) k_s2m_f32(const float *lxyz, int64_t n_pts, const int32_t *perm,
-                                                 const float2 *x, const int32_t *leaf_cell,
-                                                 const int32_t *leaf_begin, const int32_t *leaf_end,
-                                                 double w, const double *dir, double kappa, float *mom,
-                                                 int64_t ncell, int KP, float *maxabs) {
+__global__ void __launch_bounds__(128) k_s2m_tc(const double *xyz, int64_t n_pts, const int32_t *perm,
+                                                const float2 *x, const int32_t *leaf_cell,
+                                                const int32_t *leaf_begin, const int32_t *leaf_end, double lo0,
+                                                double lo1, double lo2, double w, int g, const double *dir,
+                                                double kappa, float *mom, int64_t ncell, int KP, float *maxabs) {
   constexpr int N = O * O * O;
   constexpr int CH = 32;
   constexpr int PER = (N + 127) / 128;
-  __shared__ float sl[3][CH][O];
-  __shared__ float2 sq[CH];
+  __shared__ double sl[3][CH][O];
+  __shared__ double2 sq[CH];
   const int leaf = blockIdx.x, slot = blockIdx.y;
   const int cell = leaf_cell[leaf];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const double m0 = lo0 + (cx + 0.5) * w, m1 = lo1 + (cy + 0.5) * w, m2 = lo2 + (cz + 0.5) * w;
   const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
-  const float inv_h = (float)(2.0 / w);
-  float2 acc[PER];
+  const double inv_h = 2.0 / w;
+  double2 acc[PER];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < PER; ++i) acc[i] = make_double2(0.0, 0.0);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   for (int p0 = b; p0 < e; p0 += CH) {
     const int cnt = min(CH, e - p0);
     if (threadIdx.x < cnt) {
       const int p = p0 + threadIdx.x;
-      const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
-      lagrange1f<O>(y0 * inv_h, sl[0][threadIdx.x]);
-      lagrange1f<O>(y1 * inv_h, sl[1][threadIdx.x]);
-      lagrange1f<O>(y2 * inv_h, sl[2][threadIdx.x]);
-      const float2 ph = cexpi_reduced(-kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
+      const double y0 = xyz[p] - m0, y1 = xyz[n_pts + p] - m1, y2 = xyz[2 * n_pts + p] - m2;
+      lagrange1d<O>(y0 * inv_h, sl[0][threadIdx.x]);
+      lagrange1d<O>(y1 * inv_h, sl[1][threadIdx.x]);
+      lagrange1d<O>(y2 * inv_h, sl[2][threadIdx.x]);
+      double sn = 0.0, cs = 1.0;
+      if (c0 != 0.0 || c1 != 0.0 || c2 != 0.0) sincos(-kappa * (y0 * c0 + y1 * c1 + y2 * c2), &sn, &cs);
       const float2 v = x[perm[p]];
-      sq[threadIdx.x] = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+      sq[threadIdx.x] = make_double2(cs * v.x - sn * v.y, cs * v.y + sn * v.x);
     }
     __syncthreads();
 #pragma unroll
@@ -161,9 +160,9 @@ __global__ void __launch_bounds__(128) k_s2m_f32(const float *lxyz, int64_t n_pt
       if (k < N) {
         const int kx = k % O, ky = (k / O) % O, kz = k / (O * O);
         for (int q = 0; q < cnt; ++q) {
-          const float l = sl[0][q][kx] * sl[1][q][ky] * sl[2][q][kz];
-          acc[i].x = fmaf(l, sq[q].x, acc[i].x);
-          acc[i].y = fmaf(l, sq[q].y, acc[i].y);
+          const double l = sl[0][q][kx] * sl[1][q][ky] * sl[2][q][kz];
+          acc[i].x = fma(l, sq[q].x, acc[i].x);
+          acc[i].y = fma(l, sq[q].y, acc[i].y);
         }
       }
     }
@@ -175,13 +174,89 @@ __global__ void __launch_bounds__(128) k_s2m_f32(const float *lxyz, int64_t n_pt
   for (int i = 0; i < PER; ++i) {
     const int k = threadIdx.x + 128 * i;
     if (k < N) {
-      dst[k] = acc[i].x;
-      dst[N + k] = acc[i].y;
-      mx = fmaxf(mx, fmaxf(abs_or_inf(acc[i].x), abs_or_inf(acc[i].y)));
+      const float re = (float)acc[i].x, im = (float)acc[i].y;
+      dst[k] = re;
+      dst[N + k] = im;
+      mx = fmaxf(mx, fmaxf(abs_or_inf(re), abs_or_inf(im)));
     }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0.f) atomic_max_abs(maxabs, mx);
+}
+
+// S2M for leaves of at most kSmallLeafS2M points: one warp per (leaf, slot),
+// lanes over the n coefficients; the point's 3 o basis values are computed
+// once (one lane each) and shared through shared memory; FP64 throughout.
+constexpr int kSmallLeafS2M = 16;
+
+template <int O>
+__global__ void __launch_bounds__(256) k_s2m_small(const double *xyz, int64_t n_pts, const int32_t *perm,
+                                                   const float2 *x, const int32_t *leaf_cell,
+                                                   const int32_t *leaf_begin, const int32_t *leaf_end,
+                                                   int64_t nleaves, int nslots, double lo0, double lo1, double lo2,
+                                                   double w, int g, const double *dir, double kappa, float *mom,
+                                                   int64_t ncell, int KP, float *maxabs) {
+  constexpr int N = O * O * O;
+  constexpr int KPL = (N + 31) / 32;
+  __shared__ double sb[8][3 * O + 2];         // per warp: basis values, then the phased x value
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (gw >= nleaves * nslots) return;
+  const int64_t leaf = gw / nslots;
+  const int slot = (int)(gw - leaf * nslots);
+  const int cell = leaf_cell[leaf];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const double m0 = lo0 + (cx + 0.5) * w, m1 = lo1 + (cy + 0.5) * w, m2 = lo2 + (cz + 0.5) * w;
+  const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
+  const double inv_h = 2.0 / w;
+  double ar[KPL], ai[KPL];
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) ar[j] = ai[j] = 0.0;
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  for (int p = b; p < e; ++p) {
+    const double y0 = xyz[p] - m0, y1 = xyz[n_pts + p] - m1, y2 = xyz[2 * n_pts + p] - m2;
+    if (lane < 3 * O) {
+      const int ax = lane / O, nu = lane - ax * O;
+      const double t = (ax == 0 ? y0 : ax == 1 ? y1 : y2) * inv_h;
+      double v = c_lagw[nu];
+#pragma unroll
+      for (int mu = 0; mu < O; ++mu)
+        if (mu != nu) v *= (t - c_cheb[mu]);
+      sb[wib][lane] = v;
+    } else if (lane == 31) {
+      double sn = 0.0, cs = 1.0;
+      if (c0 != 0.0 || c1 != 0.0 || c2 != 0.0) sincos(-kappa * (y0 * c0 + y1 * c1 + y2 * c2), &sn, &cs);
+      const float2 v = x[perm[p]];
+      sb[wib][3 * O] = cs * v.x - sn * v.y;
+      sb[wib][3 * O + 1] = cs * v.y + sn * v.x;
+    }
+    __syncwarp();
+    const double qr = sb[wib][3 * O], qi = sb[wib][3 * O + 1];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+      const int k = lane + 32 * j;
+      if (k < N) {
+        const double l = sb[wib][k % O] * sb[wib][O + (k / O) % O] * sb[wib][2 * O + k / (O * O)];
+        ar[j] = fma(l, qr, ar[j]);
+        ai[j] = fma(l, qi, ai[j]);
+      }
+    }
+    __syncwarp();
+  }
+  float mx = 0.f;
+  float *dst = mom + ((int64_t)slot * ncell + cell) * KP;
+#pragma unroll
+  for (int j = 0; j < KPL; ++j) {
+    const int k = lane + 32 * j;
+    if (k < N) {
+      const float re = (float)ar[j], im = (float)ai[j];
+      dst[k] = re;
+      dst[N + k] = im;
+      mx = fmaxf(mx, fmaxf(abs_or_inf(re), abs_or_inf(im)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.f) atomic_max_abs(maxabs, mx);
 }
 
 // ------------------------------------------------------ M2M / L2L (FP32)
@@ -834,75 +909,77 @@ __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(128)
   if (warp == 1) ptx::tmem_dealloc_pair(tmem, 512);
 }
 
-// ----------------------------------------------------------------- L2T
-// Knuth's TwoSum: s + t = u + err exactly in round-to-nearest; the rounding
-// errors of a running sum are collected in c (compensated summation).
-__device__ __forceinline__ void two_sum_acc(float &s, float t, float &c) {
-  const float u = __fadd_rn(s, t);
-  const float bp = __fsub_rn(u, s);
-  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(u, bp)), __fsub_rn(t, bp)));
-  s = u;
+template <int O>
+__device__ __forceinline__ double pick(const double *a, int i) {
+  double v = a[0];
+#pragma unroll
+  for (int j = 1; j < O; ++j) v = (i == j) ? a[j] : v;
+  return v;
 }
 
-// One block per leaf, one thread per target point.  The leaf's local
-// coefficients of one direction slot are staged in shared memory (read as
-// broadcasts); each point's n-term sum uses FP32 products and a compensated
-// FP32 sum (the plain FP32 sum would lose ~sqrt(n) roundings to cancellation),
-// then the slot's plane wave exp(i kappa <x - m_t, c>) with an FP64 argument.
+// ----------------------------------------------------------------- L2T
+// y_x = sum_c exp(i kappa <x - m_t, c>) sum_k L_k(x) g~_{t,c}[k] (Eq. 14,
+// centred phases), from the FP64 point coordinates and the FP64 locals, all in
+// FP64.  Leaves of more than kSmallLeaf points: one block per leaf, one
+// thread per target point, the leaf's coefficients of one slot staged in
+// shared memory (broadcast reads).
 template <int O>
-__global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
-                                                 const int32_t *leaf_begin, const int32_t *leaf_end, double w,
-                                                 const double *dir, int nslots, double kappa, const double *loc,
-                                                 int64_t ncell, int KP, float2 *ysorted) {
+__global__ void __launch_bounds__(128) k_l2t_tc(const double *xyz, int64_t n_pts, const int32_t *leaf_cell,
+                                                const int32_t *leaf_begin, const int32_t *leaf_end, double lo0,
+                                                double lo1, double lo2, double w, int g, const double *dir,
+                                                int nslots, double kappa, const double *loc, int64_t ncell, int KP,
+                                                float2 *ysorted) {
   constexpr int N = O * O * O;
-  __shared__ float g[2 * N];
+  __shared__ double gs[2 * N];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
-  const float inv_h = (float)(2.0 / w);
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const double m0 = lo0 + (cx + 0.5) * w, m1 = lo1 + (cy + 0.5) * w, m2 = lo2 + (cz + 0.5) * w;
+  const double inv_h = 2.0 / w;
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   for (int p0 = b; p0 < e; p0 += blockDim.x) {
     const int p = p0 + threadIdx.x;
     const bool act = p < e;
-    float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-    float lx[O], ly[O], lz[O];
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
     if (act) {
-      y0 = lxyz[p];
-      y1 = lxyz[n_pts + p];
-      y2 = lxyz[2 * n_pts + p];
+      y0 = xyz[p] - m0;
+      y1 = xyz[n_pts + p] - m1;
+      y2 = xyz[2 * n_pts + p] - m2;
     }
-    lagrange1f<O>(y0 * inv_h, lx);
-    lagrange1f<O>(y1 * inv_h, ly);
-    lagrange1f<O>(y2 * inv_h, lz);
+    double lx[O], ly[O], lz[O];
+    lagrange1d<O>(y0 * inv_h, lx);
+    lagrange1d<O>(y1 * inv_h, ly);
+    lagrange1d<O>(y2 * inv_h, lz);
     double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
       const double *src = loc + ((int64_t)slot * ncell + cell) * KP;
       __syncthreads();
-      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) g[i] = (float)src[i < N ? i : KP / 2 + (i - N)];
+      for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) gs[i] = src[i < N ? i : KP / 2 + (i - N)];
       __syncthreads();
-      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-#pragma unroll
+      double re = 0.0, im = 0.0;
+#pragma unroll 1
       for (int kz = 0; kz < O; ++kz) {
 #pragma unroll
         for (int ky = 0; ky < O; ++ky) {
-          const float lyz = ly[ky] * lz[kz];
+          const double lyz = ly[ky] * pick<O>(lz, kz);
           const int k0 = O * (ky + O * kz);
 #pragma unroll
           for (int kx = 0; kx < O; ++kx) {
-            const float l = lx[kx] * lyz;
-            two_sum_acc(sr, __fmul_rn(l, g[k0 + kx]), cr);
-            two_sum_acc(si, __fmul_rn(l, g[N + k0 + kx]), ci);
+            const double l = lx[kx] * lyz;
+            re = fma(l, gs[k0 + kx], re);
+            im = fma(l, gs[N + k0 + kx], im);
           }
         }
       }
-      const double re = (double)sr + (double)cr, im = (double)si + (double)ci;
       const double c0 = dir[3 * slot], c1 = dir[3 * slot + 1], c2 = dir[3 * slot + 2];
       if (c0 == 0.0 && c1 == 0.0 && c2 == 0.0) {
         tx += re;
         ty += im;
       } else {
-        const float2 ph = cexpi_reduced(kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
-        tx += re * ph.x - im * ph.y;
-        ty += re * ph.y + im * ph.x;
+        double sn, cs;
+        sincos(kappa * (y0 * c0 + y1 * c1 + y2 * c2), &sn, &cs);
+        tx += re * cs - im * sn;
+        ty += re * sn + im * cs;
       }
     }
     if (act) ysorted[p] = make_float2((float)tx, (float)ty);
@@ -910,51 +987,58 @@ __global__ void __launch_bounds__(128) k_l2t_f32(const float *lxyz, int64_t n_pt
 }
 
 // Leaves of at most kSmallLeaf points (uniform trees: ~2 points a leaf): one
-// warp per leaf, lanes over the n coefficients of one point at a time (each
-// lane a TwoSum over its n / 32 terms), partial sums reduced across the warp
-// in FP64.
-template <int O>
-__device__ __forceinline__ float pick(const float *a, int i) {
-  float v = a[0];
-#pragma unroll
-  for (int j = 1; j < O; ++j) v = (i == j) ? a[j] : v;
-  return v;
-}
+// warp per leaf, lanes over the n coefficients of one point at a time,
+// partial sums reduced across the warp; all in FP64.
 
 template <int O>
-__global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_pts, const int32_t *leaf_cell,
+__global__ void __launch_bounds__(256) k_l2t_small(const double *xyz, int64_t n_pts, const int32_t *leaf_cell,
                                                    const int32_t *leaf_begin, const int32_t *leaf_end,
-                                                   int64_t nleaves, double w, const double *dir, int nslots,
-                                                   double kappa, const double *loc, int64_t ncell, int KP,
-                                                   float2 *ysorted) {
+                                                   int64_t nleaves, double lo0, double lo1, double lo2, double w,
+                                                   int g, const double *dir, int nslots, double kappa,
+                                                   const double *loc, int64_t ncell, int KP, float2 *ysorted) {
   constexpr int N = O * O * O;
   constexpr int KPL = (N + 31) / 32;
+  __shared__ double sb[8][3 * O];             // per warp: the point's 1-D basis values
   const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (leaf >= nleaves) return;
   const int cell = leaf_cell[leaf];
-  const float inv_h = (float)(2.0 / w);
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const double m[3] = {lo0 + (cx + 0.5) * w, lo1 + (cy + 0.5) * w, lo2 + (cz + 0.5) * w};
+  const double inv_h = 2.0 / w;
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   for (int p = b; p < e; ++p) {
-    const float y0 = lxyz[p], y1 = lxyz[n_pts + p], y2 = lxyz[2 * n_pts + p];
-    float lx[O], ly[O], lz[O];
-    lagrange1f<O>(y0 * inv_h, lx);
-    lagrange1f<O>(y1 * inv_h, ly);
-    lagrange1f<O>(y2 * inv_h, lz);
+    const double y0 = xyz[p] - m[0], y1 = xyz[n_pts + p] - m[1], y2 = xyz[2 * n_pts + p] - m[2];
+    // lane a * O + nu computes L_nu along axis a (one FP64 product chain per lane)
+    if (lane < 3 * O) {
+      const int ax = lane / O, nu = lane - ax * O;
+      const double t = (ax == 0 ? y0 : ax == 1 ? y1 : y2) * inv_h;
+      double v = c_lagw[nu];
+#pragma unroll
+      for (int mu = 0; mu < O; ++mu)
+        if (mu != nu) v *= (t - c_cheb[mu]);
+      sb[wib][lane] = v;
+    }
+    __syncwarp();
+    double l[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+      const int k = lane + 32 * j;
+      l[j] = (k < N) ? sb[wib][k % O] * sb[wib][O + (k / O) % O] * sb[wib][2 * O + k / (O * O)] : 0.0;
+    }
+    __syncwarp();
     double tx = 0.0, ty = 0.0;
     for (int slot = 0; slot < nslots; ++slot) {
       const double *src = loc + ((int64_t)slot * ncell + cell) * KP;
-      float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+      double re = 0.0, im = 0.0;
 #pragma unroll
       for (int j = 0; j < KPL; ++j) {
         const int k = lane + 32 * j;
         if (k < N) {
-          const float l = pick<O>(lx, k % O) * pick<O>(ly, (k / O) % O) * pick<O>(lz, k / (O * O));
-          two_sum_acc(sr, __fmul_rn(l, (float)src[k]), cr);
-          two_sum_acc(si, __fmul_rn(l, (float)src[KP / 2 + k]), ci);
+          re = fma(l[j], src[k], re);
+          im = fma(l[j], src[KP / 2 + k], im);
         }
       }
-      double re = (double)sr + (double)cr, im = (double)si + (double)ci;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -965,9 +1049,10 @@ __global__ void __launch_bounds__(256) k_l2t_small(const float *lxyz, int64_t n_
         tx += re;
         ty += im;
       } else {
-        const float2 ph = cexpi_reduced(kappa * ((double)y0 * c0 + (double)y1 * c1 + (double)y2 * c2));
-        tx += re * ph.x - im * ph.y;
-        ty += re * ph.y + im * ph.x;
+        double sn, cs;
+        sincos(kappa * (y0 * c0 + y1 * c1 + y2 * c2), &sn, &cs);
+        tx += re * cs - im * sn;
+        ty += re * sn + im * cs;
       }
     }
     if (lane == 0) ysorted[p] = make_float2((float)tx, (float)ty);
@@ -1062,6 +1147,95 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
       if (act[u]) {
         const float2 f = ysorted[p];
         y[tperm[p]] = make_float2((float)(ar[u] + (double)f.x), (float)(ai[u] + (double)f.y));
+      }
+    }
+  }
+}
+
+// Nearfield for several right-hand sides (leaves above kSmallLeaf points):
+// one block per target leaf, one thread per target point (strided), and per
+// pass kP2pRG right-hand sides: each pair's kernel value f(x, y) is formed
+// once and multiplied into every right-hand side of the pass.  Sources
+// (positions and the pass's x values) are staged through shared memory in
+// chunks of the block size; chunk sums in FP32 are added into FP64.
+constexpr int kP2pRG = 8;
+
+__global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, const int32_t *tperm,
+                                                  const int32_t *leaf_cell, const int32_t *leaf_begin,
+                                                  const int32_t *leaf_end, const float *sl, int64_t ns,
+                                                  const int32_t *sperm, const int32_t *s_leaf_of_cell,
+                                                  const int32_t *sb, const int32_t *se, int g, float w,
+                                                  const int32_t *near_off, int nnear, float kappa, const float2 *x,
+                                                  int nrhs, const float2 *ysorted, float2 *y) {
+  __shared__ float4 sp[128];
+  __shared__ float2 sv[kP2pRG][128];
+  const int leaf = blockIdx.x;
+  const int cell = leaf_cell[leaf];
+  const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
+  const int b = leaf_begin[leaf], e = leaf_end[leaf];
+  const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  for (int p0 = b; p0 < e; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const bool act = p < e;
+    const float px = act ? tl[p] : 0.f, py = act ? tl[nt + p] : 0.f, pz = act ? tl[2 * nt + p] : 0.f;
+    for (int r0 = 0; r0 < nrhs; r0 += kP2pRG) {
+      const int rn = min(kP2pRG, nrhs - r0);
+      double ar[kP2pRG], ai[kP2pRG];
+#pragma unroll
+      for (int r = 0; r < kP2pRG; ++r) ar[r] = ai[r] = 0.0;
+      for (int i = 0; i < nnear; ++i) {
+        const int dx = near_off[3 * i], dy = near_off[3 * i + 1], dz = near_off[3 * i + 2];
+        const int sx = cx - dx, sy = cy - dy, sz = cz - dz;
+        if (sx < 0 || sy < 0 || sz < 0 || sx >= g || sy >= g || sz >= g) continue;
+        const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
+        if (s < 0) continue;
+        const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
+        for (int q0 = sb[s]; q0 < se[s]; q0 += blockDim.x) {
+          const int cnt = min((int)blockDim.x, se[s] - q0);
+          __syncthreads();
+          if (threadIdx.x < cnt) {
+            const int q = q0 + threadIdx.x;
+            sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
+            const int64_t src = sperm[q];
+#pragma unroll
+            for (int r = 0; r < kP2pRG; ++r)
+              sv[r][threadIdx.x] = (r < rn) ? x[(int64_t)(r0 + r) * ns + src] : make_float2(0.f, 0.f);
+          }
+          __syncthreads();
+          float cr[kP2pRG], ci[kP2pRG];
+#pragma unroll
+          for (int r = 0; r < kP2pRG; ++r) cr[r] = ci[r] = 0.f;
+          for (int k = 0; k < cnt; ++k) {
+            const float4 q = sp[k];
+            const float d0 = px - q.x, d1 = py - q.y, d2 = pz - q.z;
+            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+            // coincident points (zero diagonal) and idle threads add 0
+            const float ir = (r2 > 0.f && act) ? rsqrtf(r2) : 0.f;
+            float sn, cs;
+            sincosf(kappa * (r2 * ir), &sn, &cs);
+            const float fr = inv4pi * ir * cs, fi = inv4pi * ir * sn;
+#pragma unroll
+            for (int r = 0; r < kP2pRG; ++r) {
+              const float2 v = sv[r][k];
+              cr[r] = fmaf(fr, v.x, fmaf(-fi, v.y, cr[r]));
+              ci[r] = fmaf(fr, v.y, fmaf(fi, v.x, ci[r]));
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < kP2pRG; ++r) {
+            ar[r] += (double)cr[r];
+            ai[r] += (double)ci[r];
+          }
+        }
+      }
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < kP2pRG; ++r) {
+          if (r < rn) {
+            const float2 f = ysorted[(int64_t)(r0 + r) * nt + p];
+            y[(int64_t)(r0 + r) * nt + tperm[p]] = make_float2((float)(ar[r] + (double)f.x), (float)(ai[r] + (double)f.y));
+          }
+        }
       }
     }
   }
@@ -1253,13 +1427,6 @@ void build_tc(Plan &plan, cudaStream_t st) {
     chebyshev_tables(o, cheb, lagw);
     DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_cheb, cheb, sizeof(cheb)));
     DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_lagw, lagw, sizeof(lagw)));
-    float cf[kMaxOrder], lf[kMaxOrder];
-    for (int i = 0; i < kMaxOrder; ++i) {
-      cf[i] = (float)cheb[i];
-      lf[i] = (float)lagw[i];
-    }
-    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_chebf, cf, sizeof(cf)));
-    DFDM_CUDA_TRY(cudaMemcpyToSymbol(c_lagwf, lf, sizeof(lf)));
     std::vector<double> e1d(2 * o * o);
     DFDM_CUDA_TRY(cudaMemcpy(e1d.data(), plan.e1, e1d.size() * 8, cudaMemcpyDeviceToHost));
     std::vector<float> e1f(e1d.begin(), e1d.end());
@@ -1307,7 +1474,7 @@ void build_tc(Plan &plan, cudaStream_t st) {
                                                              plan.root_lo[0], plan.root_lo[1], plan.root_lo[2], wl,
                                                              1 << p, T.sl);
   DFDM_LAUNCH_CHECK();
-  T.ysorted = plan.alloc<float2>(plan.tt.n);
+  T.ysorted = plan.alloc<float2>((size_t)plan.tt.n * plan.params.nrhs_max);   // far field per right-hand side
   // grids
   T.mom32.assign(p + 1, nullptr);
   T.loc64.assign(p + 1, nullptr);
@@ -1419,8 +1586,10 @@ void build_tc(Plan &plan, cudaStream_t st) {
   DFDM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+// One right-hand side: far field into ys (sorted target order), then, when
+// `near` is set, the nearfield and the output y in the caller's order.
 template <int O, int NP>
-static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) {
+static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, float2 *ys, bool near, cudaStream_t st) {
   constexpr int N = O * O * O;
   TcState &T = *plan.tc;
   Timing &tm = plan.timing;
@@ -1440,9 +1609,16 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
       const size_t bytes = P.slot_dir.size() * ((size_t)1 << (3 * p)) * KP * sizeof(float);
       DFDM_CUDA_TRY(cudaMemsetAsync(T.mom32[p], 0, bytes, st));
       if (nsl > 0 && ts.nleaves > 0) {
-        k_s2m_f32<O><<<dim3((unsigned)ts.nleaves, nsl), 128, 0, st>>>(
-            T.sl, ts.n, ts.perm, x, ts.leaf_cell, ts.leaf_begin, ts.leaf_end, P.w,
-            plan.dir_vec_dev + plan.dir_vec_off[p], plan.kappa, T.mom32[p], 1ll << (3 * p), KP, T.maxabs + p);
+        if (ts.max_leaf_size <= kSmallLeafS2M)
+          k_s2m_small<O><<<nblk(ts.nleaves * nsl * 32, 256), 256, 0, st>>>(
+              ts.xyz, ts.n, ts.perm, x, ts.leaf_cell, ts.leaf_begin, ts.leaf_end, ts.nleaves, nsl,
+              plan.root_lo[0], plan.root_lo[1], plan.root_lo[2], P.w, P.grid, plan.dir_vec_dev + plan.dir_vec_off[p],
+              plan.kappa, T.mom32[p], 1ll << (3 * p), KP, T.maxabs + p);
+        else
+        k_s2m_tc<O><<<dim3((unsigned)ts.nleaves, nsl), 128, 0, st>>>(
+            ts.xyz, ts.n, ts.perm, x, ts.leaf_cell, ts.leaf_begin, ts.leaf_end, plan.root_lo[0], plan.root_lo[1],
+            plan.root_lo[2], P.w, P.grid, plan.dir_vec_dev + plan.dir_vec_off[p], plan.kappa, T.mom32[p],
+            1ll << (3 * p), KP, T.maxabs + p);
         DFDM_COUNT_LAUNCH(plan);
       }
     }
@@ -1510,26 +1686,29 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
     PhaseScope sc(tm, kPhL2T, st);
     if (nsl > 0 && tt.nleaves > 0 && tt.max_leaf_size <= kSmallLeaf) {
       k_l2t_small<O><<<nblk(tt.nleaves * 32, 256), 256, 0, st>>>(
-          T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, P.w, plan.dir_vec_dev + plan.dir_vec_off[p],
-          nsl, plan.kappa, T.loc64[p], 1ll << (3 * p), KP, T.ysorted);
+          tt.xyz, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, plan.root_lo[0], plan.root_lo[1],
+          plan.root_lo[2], P.w, P.grid, plan.dir_vec_dev + plan.dir_vec_off[p], nsl, plan.kappa, T.loc64[p],
+          1ll << (3 * p), KP, ys);
       DFDM_COUNT_LAUNCH(plan);
     } else if (nsl > 0 && tt.nleaves > 0) {
-      k_l2t_f32<O><<<(unsigned)tt.nleaves, 128, 0, st>>>(T.tl, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, P.w,
-                                                         plan.dir_vec_dev + plan.dir_vec_off[p], nsl, plan.kappa,
-                                                         T.loc64[p], 1ll << (3 * p), KP, T.ysorted);
+      k_l2t_tc<O><<<(unsigned)tt.nleaves, 128, 0, st>>>(tt.xyz, tt.n, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
+                                                        plan.root_lo[0], plan.root_lo[1], plan.root_lo[2], P.w,
+                                                        P.grid, plan.dir_vec_dev + plan.dir_vec_off[p], nsl,
+                                                        plan.kappa, T.loc64[p], 1ll << (3 * p), KP, ys);
       DFDM_COUNT_LAUNCH(plan);
     } else {
-      DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));
+      DFDM_CUDA_TRY(cudaMemsetAsync(ys, 0, tt.n * sizeof(float2), st));
     }
   } else {
-    DFDM_CUDA_TRY(cudaMemsetAsync(T.ysorted, 0, tt.n * sizeof(float2), st));
+    DFDM_CUDA_TRY(cudaMemsetAsync(ys, 0, tt.n * sizeof(float2), st));
   }
+  if (!near) return;
   PhaseScope sc(tm, kPhNear, st);
   if (tt.max_leaf_size <= kSmallLeaf) {
     k_p2p_small<<<(unsigned)((tt.nleaves * 32 + 255) / 256), 256, 0, st>>>(
         T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, tt.nleaves, T.sl, ts.n, ts.perm,
         ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
-        (int)(plan.near_off.size() / 3), (float)plan.kappa, x, T.ysorted, y);
+        (int)(plan.near_off.size() / 3), (float)plan.kappa, x, ys, y);
   } else {
     // one block per target leaf; leaves of a few dozen points (uniform trees
     // just above the warp-per-leaf size) get one warp, large ones 4 warps
@@ -1538,23 +1717,39 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, cudaStream_t st) 
                                                     T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin,
                                                     ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
                                                     (int)(plan.near_off.size() / 3), (float)plan.kappa, x,
-                                                    T.ysorted, y);
+                                                    ys, y);
   }
   DFDM_COUNT_LAUNCH(plan);
 }
 
 void apply_tc(Plan &plan, const float2 *x, float2 *y, int nrhs, cudaStream_t st) {
+  TcState &T = *plan.tc;
+  const Tree &tt = plan.tt, &ts = plan.ts;
+  // several right-hand sides on leaves above the warp-per-leaf size: far
+  // fields one after the other, then one nearfield pass for all of them
+  const bool joint_near = nrhs > 1 && tt.max_leaf_size > kSmallLeaf;
   for (int r = 0; r < nrhs; ++r) {
-    const float2 *xr = x + (int64_t)r * plan.ts.n;
-    float2 *yr = y + (int64_t)r * plan.tt.n;
+    const float2 *xr = x + (int64_t)r * ts.n;
+    float2 *yr = y + (int64_t)r * tt.n;
+    float2 *ys = T.ysorted + (int64_t)r * tt.n;
     switch (plan.order) {
-      case 2: apply_tc_o<2, 64>(plan, xr, yr, st); break;     // 2n = 16  -> KP 64
-      case 3: apply_tc_o<3, 64>(plan, xr, yr, st); break;     // 2n = 54  -> KP 64
-      case 4: apply_tc_o<4, 128>(plan, xr, yr, st); break;    // 2n = 128 -> KP 128
-      case 5: apply_tc_o<5, 256>(plan, xr, yr, st); break;    // 2n = 250 -> KP 256
-      case 6: apply_tc_o<6, 448>(plan, xr, yr, st); break;    // 2n = 432 -> KP 448
+      case 2: apply_tc_o<2, 64>(plan, xr, yr, ys, !joint_near, st); break;     // 2n = 16  -> KP 64
+      case 3: apply_tc_o<3, 64>(plan, xr, yr, ys, !joint_near, st); break;     // 2n = 54  -> KP 64
+      case 4: apply_tc_o<4, 128>(plan, xr, yr, ys, !joint_near, st); break;    // 2n = 128 -> KP 128
+      case 5: apply_tc_o<5, 256>(plan, xr, yr, ys, !joint_near, st); break;    // 2n = 250 -> KP 256
+      case 6: apply_tc_o<6, 448>(plan, xr, yr, ys, !joint_near, st); break;    // 2n = 432 -> KP 448
       default: throw Error{DFDM_ERR_UNSUPPORTED, "tensor-core form supports orders 2..6"};
     }
+  }
+  if (joint_near) {
+    const int p = plan.depth;
+    PhaseScope sc(plan.timing, kPhNear, st);
+    const unsigned threads = (tt.n <= 64 * tt.nleaves) ? 64u : 128u;
+    k_p2p_mrhs<<<(unsigned)tt.nleaves, threads, 0, st>>>(
+        T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end, T.sl, ts.n, ts.perm, ts.leaf_of_cell,
+        ts.leaf_begin, ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
+        (int)(plan.near_off.size() / 3), (float)plan.kappa, x, nrhs, T.ysorted, y);
+    DFDM_COUNT_LAUNCH(plan);
   }
 }
 

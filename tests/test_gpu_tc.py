@@ -76,3 +76,28 @@ def test_non_finite_input_reports_numeric_error():
         y = gpu_apply(p, complex_normal(3000, 74).astype(np.complex64))
         p.check()
         assert np.all(np.isfinite(y))
+
+
+def test_tc_multi_rhs_matches_single_rhs_and_oracle():
+    """Several right-hand sides at once (leaves of ~40 points: the nearfield of
+    all right-hand sides runs as one pass, f(x, y) formed once per pair) equal
+    the products of one right-hand side at a time, and the oracle's."""
+    import torch
+    n, nrhs = 20000, 10          # 10: one full group of 8 and a partial one
+    t = uniform_points(n, 41)
+    s = uniform_points(n, 42)
+    xs = np.stack([complex_normal(n, 43 + r) for r in range(nrhs)])
+    with pkg.Plan(t, s, 30.0, order=4, max_depth=3, precision=pkg.TC_FP16X3, nrhs_max=nrhs) as plan:
+        assert plan.stats()["nf_entries"] > 0
+        xd = torch.from_numpy(xs.astype(np.complex64)).cuda()
+        y_all = plan.apply(xd).cpu().numpy()
+        plan.check()
+        for r in (0, 7, 8, 9):
+            y_one = plan.apply(xd[r]).cpu().numpy()
+            assert rel_l2(y_all[r], y_one) < 1e-6, r
+    o = FDMOracle(t, s, 30.0, 4, [0, 0, 0], 1.0, 3)
+    rows = np.arange(0, n, 97)
+    for r in (0, 9):
+        err = rel_l2(y_all[r][rows], o.apply(xs[r], rows=rows))
+        print("multi-RHS TC vs oracle rel l2 (rhs %d) = %.3e" % (r, err))
+        assert err < TOL_TC

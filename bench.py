@@ -153,6 +153,55 @@ def _traffic(workload_name):
     return float(fields["dram bytes per product"])
 
 
+def _fp64_comparator(workload_name):
+    """The plain FP64 form's products/s on this workload, from its measured
+    summary under profiles/ (one product takes minutes, so it is measured
+    once, not every run) -- None when there is none."""
+    path = os.path.join(ROOT, "profiles", "fp64_comparator_%s.md" % workload_name)
+    if not os.path.exists(path):
+        return None
+    out = {"source": os.path.relpath(path, ROOT)}
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) != 2:
+            continue
+        if cells[0] == "time per product":
+            out["s_per_product"] = float(cells[1].split()[0])
+            out["value"] = 1.0 / out["s_per_product"]
+            out["unit"] = UNIT
+        elif cells[0] == "clocks":
+            out["clocks"] = cells[1]
+        elif cells[0].startswith("rel-l2 against"):
+            out["rel_err_vs_oracle_rows"] = float(cells[1].split()[0])
+    return out if "value" in out else None
+
+
+def _blas_threads():
+    """Threads numpy's BLAS may use (the O_fdm oracle's only parallelism)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except ImportError:
+        pass
+    return len(os.sched_getaffinity(0))
+
+
+def _oracle_fdm_rate(targets, sources, kappa, order, depth, x, nrows):
+    """O_fdm (Alg. 4, FP64 numpy oracle) on the host: plan setup, then the
+    whole upward pass and the downward pass restricted to nrows sampled rows.
+    A full product costs at least this, so 1 / time bounds its rate from above."""
+    from oracle.fdm import FDMOracle
+    rows = sample_rows(targets.shape[0], nrows, seed=5)
+    t0 = time.perf_counter()
+    o = FDMOracle(targets, sources, kappa, order, [0, 0, 0], 1.0, depth)
+    t1 = time.perf_counter()
+    o.apply(x, rows=rows)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
 def _oracle_rows_per_sec(targets, sources, kappa, x, nrows):
     from oracle.direct import direct_rows, direct_threads
     rows = sample_rows(targets.shape[0], nrows, seed=5)
@@ -325,12 +374,26 @@ def run_ours(args):
             "setup_s": setup_s, "n_coupling": st["n_coupling"], "n_stored_coupling": st["n_stored_coupling"],
             "n_coupling_per_level": st["level_coupling"][:w["depth"] + 1],
             "rel_err_vs_oracle_rows": err, "clocks": clocks}
+    if prec == pkg.TC_FP16X3:
+        cmp64 = _fp64_comparator(args.workload)
+        if cmp64 is not None:
+            cmp64["tc_over_fp64"] = value / world / cmp64["value"]
+        line["fp64_comparator"] = cmp64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rps, dt, cores = _oracle_rows_per_sec(t, s, w["kappa"], x, args.ref_rows)
         line["cpu_baseline"] = {"value": rps / w["n"], "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "O_direct (FP64 C double loop, OpenMP) on %d target rows x all %d "
                                           "sources (%.1f s), scaled to the full product"
                                           % (args.ref_rows, w["n"], dt)}
+    if rank == 0 and world == 1 and args.fdm_baseline > 0:
+        setup, apply_s = _oracle_fdm_rate(t, s, w["kappa"], w["order"], w["depth"], x, args.fdm_baseline)
+        line["cpu_baseline_fdm"] = {"value": 1.0 / apply_s, "unit": UNIT, "bound": "upper",
+                                    "cores": _blas_threads(),
+                                    "kind": "oracle", "setup_s": setup,
+                                    "sample": "O_fdm (Alg. 4, FP64 numpy) on the host: full upward pass, "
+                                              "downward pass to %d sampled rows (%.1f s; plan %.1f s); a "
+                                              "full product takes at least this long" % (args.fdm_baseline,
+                                                                                        apply_s, setup)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -447,6 +510,98 @@ def run_batch(args):
     return 0
 
 
+SEL_KAPPAS = (32.0, 128.0, 256.0)
+SEL_TOLS = (1e-3, 1e-5, 1e-7)
+SEL_N, SEL_DEPTH = 1 << 21, 6
+FP64_M2L_TFLOPS = 0.62        # measured rate of k_m2l_fp64 (4M workload, one product)
+
+
+def run_selector_study(args):
+    """The learned selector against the fixed rule at 2^21 points.
+
+    Training: selector_problems(args.sel_train, kappa 2..96, depths 3 and 4),
+    each measured at orders 2..7 and two l_hf (selector_data.measure), samples
+    at 57 tolerances 1e-1..1e-8 per level, full-batch Adam for 2000 epochs on
+    the GPU.  Fixed rule: per tolerance the smallest order whose error stays
+    below tol / 3 on every training problem, with the default l_hf.  Test:
+    2^21 uniform targets and sources (seeds 1, 2), depth 6, x seed 3, kappa in
+    {32, 128, 256}, tol in {1e-3, 1e-5, 1e-7}; each choice is applied once
+    after a warm-up (tensor-core form for tol >= 1e-6 and order <= 6, FP64
+    otherwise) and scored on 2048 exact rows of Eq. (1).  One JSON line per
+    cell, then a summary line."""
+    import torch
+
+    import paper_2004_14229_gb300 as pkg
+    from paper_2004_14229_gb300 import selector_data as D
+    from paper_2004_14229_gb300.workloads import (complex_normal, selector_init, selector_problems,
+                                                  uniform_points)
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    train = D.measure(selector_problems(args.sel_train, seed0=200, kappa_range=(2.0, 96.0), depths=(3, 4)))
+    t_measure = time.perf_counter() - t0
+    tols = np.logspace(-1, -8, 57)
+    X, T = D.make_samples(train, tols)
+    sel, losses = pkg.Selector.train(selector_init(), X, T, epochs=2000, lr=3e-3)
+    fixed = {}
+    for tol in SEL_TOLS:
+        fixed[tol] = max(D.labels(r, tol)[0] for r in train)
+    print(json.dumps({"selector_training": {"problems": len(train), "samples": int(X.shape[0]),
+                                            "measure_s": t_measure, "loss_first": float(losses[0]),
+                                            "loss_last": float(losses[-1]),
+                                            "fixed_rule_order": {str(k): v for k, v in fixed.items()}}}),
+          flush=True)
+
+    t = uniform_points(SEL_N, 1)
+    s = uniform_points(SEL_N, 2)
+    x = complex_normal(SEL_N, 3)
+    xd64 = torch.from_numpy(x).cuda()
+    xd32 = xd64.to(torch.complex64)
+    rows = sample_rows(SEL_N, 2048, seed=4)
+    td, sd = torch.from_numpy(t).cuda(), torch.from_numpy(s).cuda()
+    summary = []
+    for kappa in SEL_KAPPAS:
+        ref = pkg.direct_rows(td, sd, kappa, xd64, torch.from_numpy(rows).cuda()).cpu().numpy()
+        with pkg.Plan(t, s, kappa, order=2, max_depth=SEL_DEPTH, precision=pkg.FP64) as probe:
+            lhf0 = probe.stats()["l_hf"]
+        for tol in SEL_TOLS:
+            o_sel, lhf_sel = sel.select(kappa, tol, SEL_N, SEL_DEPTH)
+            cell = {"kappa": kappa, "tol": tol}
+            for who, order, lhf in (("selector", o_sel, lhf_sel), ("fixed", fixed[tol], lhf0)):
+                order = min(max(order, 2), 10)
+                tc = tol >= 1e-6 and order <= 6
+                prec = pkg.TC_FP16X3 if tc else pkg.FP64
+                r = {"order": order, "l_hf": lhf, "form": "tc" if tc else "fp64", "nodes_per_box": order ** 3}
+                with pkg.Plan(t, s, kappa, order=order, max_depth=SEL_DEPTH, l_hf=lhf, precision=prec) as pl:
+                    st = pl.stats()
+                    est = 8.0 * order ** 6 * st["n_coupling"] / (FP64_M2L_TFLOPS * 1e12)
+                    if not tc and est > args.sel_fp64_cap:
+                        r["skipped"] = "FP64 M2L estimated at %.0f s (cap %.0f s)" % (est, args.sel_fp64_cap)
+                    else:
+                        xin = xd32 if tc else xd64
+                        y = pl.apply(xin)
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        pl.apply(xin, y)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        pl.check()
+                        yr = y.cpu().numpy()[rows].astype(np.complex128)
+                        r["err"] = float(np.linalg.norm(yr - ref) / np.linalg.norm(ref))
+                        r["meets_tol"] = r["err"] <= tol
+                        r["ms"] = e0.elapsed_time(e1)
+                    r["n_coupling"] = st["n_coupling"]
+                cell[who] = r
+            print(json.dumps({"selector_study_cell": cell}), flush=True)
+            summary.append(cell)
+    print(json.dumps({"selector_study": {"n": SEL_N, "depth": SEL_DEPTH, "direct_rows": int(rows.size),
+                                         "cells": len(summary), "total_s": time.perf_counter() - t0}}),
+          flush=True)
+    return 0
+
+
 def _free_port():
     import socket
     with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
@@ -473,9 +628,16 @@ def main():
     ap.add_argument("--precision", default="tc", choices=["tc", "fp64"])
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fdm-baseline", type=int, default=0,
+                    help="also time the O_fdm oracle on the host, downward pass to this many rows")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="products timed end to end through dfdm_apply_host (0: none)")
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
+    ap.add_argument("--selector-study", action="store_true",
+                    help="train the parameter selector and compare it with the fixed rule at 2^21 points")
+    ap.add_argument("--sel-train", type=int, default=96, help="training problems of the selector study")
+    ap.add_argument("--sel-fp64-cap", type=float, default=150.0,
+                    help="skip FP64 products of the selector study whose M2L is estimated above this (s)")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return launch_replicas(args.gpus, sys.argv[1:])
@@ -484,6 +646,8 @@ def main():
         raise SystemExit("--gpus %d but %d ranks were launched" % (args.gpus, world))
     if args.impl == "reference":
         return run_reference(args)
+    if args.selector_study:
+        return run_selector_study(args)
     if args.batch > 0:
         return run_batch(args)
     return run_ours(args)

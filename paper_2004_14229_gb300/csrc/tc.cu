@@ -1082,6 +1082,7 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
   for (int p0 = b; p0 < e; p0 += kP2pT * blockDim.x) {
     float px[kP2pT], py[kP2pT], pz[kP2pT];
     double ar[kP2pT], ai[kP2pT];
@@ -1110,7 +1111,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
           const int q = q0 + threadIdx.x;
           // source position relative to the target leaf's centre
           sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
-          sv[threadIdx.x] = x[sperm[q]];
+          const float2 v = x[sperm[q]];
+          sv[threadIdx.x] = make_float2(v.x * inv4pi, v.y * inv4pi);   // x_y / (4 pi)
         }
         __syncthreads();
         // every staged source against the thread's kP2pT targets: independent
@@ -1125,13 +1127,13 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
           for (int u = 0; u < kP2pT; ++u) {
             const float d0 = px[u] - q.x, d1 = py[u] - q.y, d2 = pz[u] - q.z;
             const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            // coincident points (zero diagonal) and idle target slots add 0
-            const float ir = (r2 > 0.f && act[u]) ? rsqrtf(r2) : 0.f;
+            // coincident points (zero diagonal) add 0; idle target slots are
+            // computed and never written
+            const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
             float sn, cs;
-            sincosf(kappa * (r2 * ir), &sn, &cs);
-            const float sc = inv4pi * ir;
-            cr[u] = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr[u]);
-            ci[u] = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci[u]);
+            sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+            cr[u] = fmaf(ir, fmaf(cs, v.x, -sn * v.y), cr[u]);
+            ci[u] = fmaf(ir, fmaf(cs, v.y, sn * v.x), ci[u]);
           }
         }
 #pragma unroll
@@ -1174,6 +1176,7 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
   for (int p0 = b; p0 < e; p0 += blockDim.x) {
     const int p = p0 + threadIdx.x;
     const bool act = p < e;
@@ -1198,8 +1201,10 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
             sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
             const int64_t src = sperm[q];
 #pragma unroll
-            for (int r = 0; r < kP2pRG; ++r)
-              sv[r][threadIdx.x] = (r < rn) ? x[(int64_t)(r0 + r) * ns + src] : make_float2(0.f, 0.f);
+            for (int r = 0; r < kP2pRG; ++r) {
+              const float2 v = (r < rn) ? x[(int64_t)(r0 + r) * ns + src] : make_float2(0.f, 0.f);
+              sv[r][threadIdx.x] = make_float2(v.x * inv4pi, v.y * inv4pi);   // x_y / (4 pi)
+            }
           }
           __syncthreads();
           float cr[kP2pRG], ci[kP2pRG];
@@ -1209,11 +1214,11 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
             const float4 q = sp[k];
             const float d0 = px - q.x, d1 = py - q.y, d2 = pz - q.z;
             const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            // coincident points (zero diagonal) and idle threads add 0
-            const float ir = (r2 > 0.f && act) ? rsqrtf(r2) : 0.f;
+            // coincident points (zero diagonal) add 0; idle threads are never written
+            const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
             float sn, cs;
-            sincosf(kappa * (r2 * ir), &sn, &cs);
-            const float fr = inv4pi * ir * cs, fi = inv4pi * ir * sn;
+            sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+            const float fr = ir * cs, fi = ir * sn;
 #pragma unroll
             for (int r = 0; r < kP2pRG; ++r) {
               const float2 v = sv[r][k];
@@ -1262,6 +1267,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, 
   const int b = leaf_begin[leaf];
   const int cnt = min(kSmallLeaf, leaf_end[leaf] - b);
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
+  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
   float px[kSmallLeaf], py[kSmallLeaf], pz[kSmallLeaf], cr[kSmallLeaf], ci[kSmallLeaf];
 #pragma unroll
   for (int u = 0; u < kSmallLeaf; ++u) {
@@ -1280,7 +1286,8 @@ __global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, 
     const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
     for (int q = sb[s]; q < se[s]; ++q) {
       const float qx = sl[q] - ox, qy = sl[ns + q] - oy, qz = sl[2 * ns + q] - oz;
-      const float2 v = x[sperm[q]];
+      const float2 x0 = x[sperm[q]];
+      const float2 v = make_float2(x0.x * inv4pi, x0.y * inv4pi);   // x_y / (4 pi)
 #pragma unroll
       for (int u = 0; u < kSmallLeaf; ++u) {
         if (u >= cnt) break;
@@ -1289,10 +1296,9 @@ __global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, 
         if (r2 == 0.f) continue;   // coincident points (zero diagonal)
         const float ir = rsqrtf(r2);
         float sn, cs;
-        sincosf(kappa * (r2 * ir), &sn, &cs);
-        const float sc = inv4pi * ir;
-        cr[u] = fmaf(sc, fmaf(cs, v.x, -sn * v.y), cr[u]);
-        ci[u] = fmaf(sc, fmaf(cs, v.y, sn * v.x), ci[u]);
+        sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+        cr[u] = fmaf(ir, fmaf(cs, v.x, -sn * v.y), cr[u]);
+        ci[u] = fmaf(ir, fmaf(cs, v.y, sn * v.x), ci[u]);
       }
     }
   }

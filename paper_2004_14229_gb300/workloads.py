@@ -153,20 +153,24 @@ def selector_init(seed=SEED_SELECTOR):
     return np.concatenate(parts).astype(np.float32)
 
 
-def selector_problems(count, seed0=200, n_range=(2000, 8000), kappa_range=(2.0, 48.0)):
+def selector_problems(count, seed0=200, n_range=(2000, 8000), kappa_range=(2.0, 48.0), depths=(3,)):
     """Small problems on which the method measures its own error for the
-    selector's training data: problem i draws from default_rng(seed0 + i),
-    in order, N log-uniform in n_range, kappa log-uniform in the i-th of
-    `count` equal log-intervals of kappa_range (so the problems cover the
-    range), targets, sources (uniform in [0,1)^3), one complex vector; depth 3."""
+    selector's training data: problem i has tree depth d = depths[i % len(depths)]
+    and draws from default_rng(seed0 + i), in order, N log-uniform in
+    n_range x 8^(d - 3) (the same points per leaf box at every depth), kappa
+    log-uniform in the i-th of `count` equal log-intervals of kappa_range (so
+    the problems cover the range), targets, sources (uniform in [0,1)^3), one
+    complex vector."""
     out = []
     lk0, lk1 = np.log(kappa_range[0]), np.log(kappa_range[1])
     for i in range(int(count)):
         rng = np.random.default_rng(seed0 + i)
-        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        depth = int(depths[i % len(depths)])
+        scale = 8.0 ** (depth - 3)
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0] * scale), np.log(n_range[1] * scale)))))
         kappa = float(np.exp(lk0 + (i + rng.uniform()) * (lk1 - lk0) / count))
         t = rng.random((n, 3))
         s = rng.random((n, 3))
         z = rng.standard_normal((n, 2))
-        out.append(dict(targets=t, sources=s, kappa=kappa, max_depth=3, x=z[:, 0] + 1j * z[:, 1]))
+        out.append(dict(targets=t, sources=s, kappa=kappa, max_depth=depth, x=z[:, 0] + 1j * z[:, 1]))
     return out

@@ -261,6 +261,12 @@ def run_ours(args):
     xd = torch.from_numpy(x.astype(cdt)).cuda()
     yd = torch.empty(w["n"], dtype=tdt, device="cuda")
     stream = torch.cuda.current_stream()
+    tuning = None
+    if args.autotune and prec == pkg.TC_FP16X3:
+        # measured launch shapes, chosen before the timed region (set-up)
+        t_tune = time.perf_counter()
+        tuning = plan.autotune(xd, cache=args.tune_cache)
+        tuning["seconds"] = time.perf_counter() - t_tune
 
     for _ in range(args.warmup):
         plan.apply(xd, yd)
@@ -373,7 +379,7 @@ def run_ours(args):
             "m2l_ms_per_level": [v / args.steps for v in m2l_ms[:w["depth"] + 1]],
             "setup_s": setup_s, "n_coupling": st["n_coupling"], "n_stored_coupling": st["n_stored_coupling"],
             "n_coupling_per_level": st["level_coupling"][:w["depth"] + 1],
-            "rel_err_vs_oracle_rows": err, "clocks": clocks}
+            "rel_err_vs_oracle_rows": err, "clocks": clocks, "autotune": tuning}
     if prec == pkg.TC_FP16X3:
         cmp64 = _fp64_comparator(args.workload)
         if cmp64 is not None:
@@ -519,16 +525,18 @@ FP64_M2L_TFLOPS = 0.62        # measured rate of k_m2l_fp64 (4M workload, one pr
 def run_selector_study(args):
     """The learned selector against the fixed rule at 2^21 points.
 
-    Training: selector_problems(args.sel_train, kappa 2..96, depths 3 and 4),
-    each measured at orders 2..7 and two l_hf (selector_data.measure), samples
-    at 57 tolerances 1e-1..1e-8 per level, full-batch Adam for 2000 epochs on
-    the GPU.  Fixed rule: per tolerance the smallest order whose error stays
+    Training: selector_problems(args.sel_train, kappa 2..96, depth 3), each
+    measured at orders 2..7 and two l_hf (selector_data.measure), problems
+    taken in order until args.sel_budget seconds are spent; samples at 57
+    tolerances 1e-1..1e-8 per level; full-batch Adam for 2000 epochs on the
+    GPU.  Fixed rule: per tolerance the smallest order whose error stays
     below tol / 3 on every training problem, with the default l_hf.  Test:
     2^21 uniform targets and sources (seeds 1, 2), depth 6, x seed 3, kappa in
     {32, 128, 256}, tol in {1e-3, 1e-5, 1e-7}; each choice is applied once
     after a warm-up (tensor-core form for tol >= 1e-6 and order <= 6, FP64
-    otherwise) and scored on 2048 exact rows of Eq. (1).  One JSON line per
-    cell, then a summary line."""
+    otherwise; FP64 cells after all tensor-core cells, skipped when their M2L
+    is estimated above args.sel_fp64_cap seconds) and scored on 2048 exact
+    rows of Eq. (1).  One JSON line per cell, then a summary line."""
     import torch
 
     import paper_2004_14229_gb300 as pkg
@@ -538,7 +546,12 @@ def run_selector_study(args):
 
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    train = D.measure(selector_problems(args.sel_train, seed0=200, kappa_range=(2.0, 96.0), depths=(3, 4)))
+    train = []
+    for p in selector_problems(args.sel_train, seed0=200, kappa_range=(2.0, 96.0)):
+        if time.perf_counter() - t0 > args.sel_budget:
+            break
+        train += D.measure([p])
+        print("measured %d problems, %.0f s" % (len(train), time.perf_counter() - t0), file=sys.stderr, flush=True)
     t_measure = time.perf_counter() - t0
     tols = np.logspace(-1, -8, 57)
     X, T = D.make_samples(train, tols)
@@ -560,42 +573,54 @@ def run_selector_study(args):
     rows = sample_rows(SEL_N, 2048, seed=4)
     td, sd = torch.from_numpy(t).cuda(), torch.from_numpy(s).cuda()
     summary = []
+    refs, lhf0 = {}, {}
     for kappa in SEL_KAPPAS:
-        ref = pkg.direct_rows(td, sd, kappa, xd64, torch.from_numpy(rows).cuda()).cpu().numpy()
+        refs[kappa] = pkg.direct_rows(td, sd, kappa, xd64, torch.from_numpy(rows).cuda()).cpu().numpy()
         with pkg.Plan(t, s, kappa, order=2, max_depth=SEL_DEPTH, precision=pkg.FP64) as probe:
-            lhf0 = probe.stats()["l_hf"]
-        for tol in SEL_TOLS:
-            o_sel, lhf_sel = sel.select(kappa, tol, SEL_N, SEL_DEPTH)
-            cell = {"kappa": kappa, "tol": tol}
-            for who, order, lhf in (("selector", o_sel, lhf_sel), ("fixed", fixed[tol], lhf0)):
-                order = min(max(order, 2), 10)
-                tc = tol >= 1e-6 and order <= 6
-                prec = pkg.TC_FP16X3 if tc else pkg.FP64
-                r = {"order": order, "l_hf": lhf, "form": "tc" if tc else "fp64", "nodes_per_box": order ** 3}
+            lhf0[kappa] = probe.stats()["l_hf"]
+    cells = [(k, tol) for tol in SEL_TOLS for k in SEL_KAPPAS]
+    # tensor-core cells first, FP64 cells while the time budget lasts
+    for kappa, tol in cells:
+        ref = refs[kappa]
+        o_sel, lhf_sel = sel.select(kappa, tol, SEL_N, SEL_DEPTH)
+        cell = {"kappa": kappa, "tol": tol}
+        for who, order, lhf in (("selector", o_sel, lhf_sel), ("fixed", fixed[tol], lhf0[kappa])):
+            order = min(max(order, 2), 10)
+            tc = tol >= 1e-6 and order <= 6
+            prec = pkg.TC_FP16X3 if tc else pkg.FP64
+            r = {"order": order, "l_hf": lhf, "form": "tc" if tc else "fp64", "nodes_per_box": order ** 3}
+            # the planner's counts for the fully occupied tree (host only)
+            n_c, n_sc, _ = pkg.uniform_counts(kappa, SEL_DEPTH, l_hf=lhf)
+            est = 8.0 * order ** 6 * n_c / (FP64_M2L_TFLOPS * 1e12)
+            op_gb = 16.0 * order ** 6 * n_sc / 1e9
+            r["n_coupling"] = n_c
+            if not tc and (est > args.sel_fp64_cap or op_gb > 60.0):
+                r["skipped"] = ("FP64 M2L estimated at %.0f s (cap %.0f s), FP64 operators %.0f GB"
+                                % (est, args.sel_fp64_cap, op_gb))
+            elif not tc and time.perf_counter() - t0 > args.sel_total:
+                r["skipped"] = "study time budget (%.0f s) spent" % args.sel_total
+            else:
                 with pkg.Plan(t, s, kappa, order=order, max_depth=SEL_DEPTH, l_hf=lhf, precision=prec) as pl:
-                    st = pl.stats()
-                    est = 8.0 * order ** 6 * st["n_coupling"] / (FP64_M2L_TFLOPS * 1e12)
-                    if not tc and est > args.sel_fp64_cap:
-                        r["skipped"] = "FP64 M2L estimated at %.0f s (cap %.0f s)" % (est, args.sel_fp64_cap)
-                    else:
-                        xin = xd32 if tc else xd64
-                        y = pl.apply(xin)
-                        torch.cuda.synchronize()
-                        e0 = torch.cuda.Event(enable_timing=True)
-                        e1 = torch.cuda.Event(enable_timing=True)
-                        e0.record()
-                        pl.apply(xin, y)
-                        e1.record()
-                        torch.cuda.synchronize()
-                        pl.check()
-                        yr = y.cpu().numpy()[rows].astype(np.complex128)
-                        r["err"] = float(np.linalg.norm(yr - ref) / np.linalg.norm(ref))
-                        r["meets_tol"] = r["err"] <= tol
-                        r["ms"] = e0.elapsed_time(e1)
-                    r["n_coupling"] = st["n_coupling"]
-                cell[who] = r
-            print(json.dumps({"selector_study_cell": cell}), flush=True)
-            summary.append(cell)
+                    xin = xd32 if tc else xd64
+                    # tensor-core products after one warm-up; an FP64 product
+                    # (tens of seconds) is timed cold, once
+                    y = pl.apply(xin) if tc else torch.empty(SEL_N, dtype=torch.complex128, device="cuda")
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    pl.apply(xin, y)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    pl.check()
+                    r["n_coupling"] = pl.stats()["n_coupling"]
+                yr = y.cpu().numpy()[rows].astype(np.complex128)
+                r["err"] = float(np.linalg.norm(yr - ref) / np.linalg.norm(ref))
+                r["meets_tol"] = r["err"] <= tol
+                r["ms"] = e0.elapsed_time(e1)
+            cell[who] = r
+        print(json.dumps({"selector_study_cell": cell}), flush=True)
+        summary.append(cell)
     print(json.dumps({"selector_study": {"n": SEL_N, "depth": SEL_DEPTH, "direct_rows": int(rows.size),
                                          "cells": len(summary), "total_s": time.perf_counter() - t0}}),
           flush=True)
@@ -633,10 +658,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="products timed end to end through dfdm_apply_host (0: none)")
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=False,
+                    help="time candidate launch shapes before the timed region and keep the fastest")
+    ap.add_argument("--tune-cache", default=None, help="JSON-lines cache of the launch-shape tuner")
     ap.add_argument("--selector-study", action="store_true",
                     help="train the parameter selector and compare it with the fixed rule at 2^21 points")
-    ap.add_argument("--sel-train", type=int, default=96, help="training problems of the selector study")
-    ap.add_argument("--sel-fp64-cap", type=float, default=150.0,
+    ap.add_argument("--sel-train", type=int, default=64, help="training problems of the selector study")
+    ap.add_argument("--sel-budget", type=float, default=300.0,
+                    help="seconds the selector study may spend measuring training problems")
+    ap.add_argument("--sel-total", type=float, default=540.0,
+                    help="no FP64 cell of the selector study starts after this many seconds")
+    ap.add_argument("--sel-fp64-cap", type=float, default=110.0,
                     help="skip FP64 products of the selector study whose M2L is estimated above this (s)")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:

@@ -156,6 +156,40 @@ dfdm_status dfdm_plan_set_timing(dfdm_plan plan, int enable);
  * INVALID_ARG when timing is off or no apply ran since it was turned on. */
 dfdm_status dfdm_plan_timing(dfdm_plan plan, dfdm_timing *t);
 
+/* Launch shapes chosen by dfdm_plan_autotune and what they measured. */
+typedef struct {
+  int m2l_nsplit[16]; /* per level l: chunks the M2L operator lists of a tile
+                         are cut into (0: the level has no M2L)            */
+  int p2p_threads;    /* nearfield block size (0: small-leaf kernel, fixed) */
+  int p2p_chunks;     /* nearfield target chunks per leaf                   */
+  double rule_ms;     /* one product with the built-in rule (0: from cache) */
+  double tuned_ms;    /* one product with the chosen shapes (0: from cache) */
+  int products;       /* products timed (0: from cache)                    */
+  int from_cache;     /* 1: taken from cache_path without timing           */
+} dfdm_tuning;
+
+/* Measured tuner of the tensor-core form's launch shapes: how many chunks
+ * every level's M2L operator lists are cut into (Alg. 4, multiplication
+ * phase) and the nearfield's block size and target chunks per leaf.  A few
+ * candidates per level (the built-in rule's first) are timed on whole
+ * products of x with CUDA events on `stream` (per-level M2L and nearfield
+ * times, the better of two products per candidate, after one untimed
+ * product); the fastest per level and for the nearfield are kept, and
+ * later applies use them, unless the tuned product is slower than the
+ * rule's, in which case the rule stays.  The result does not depend on the
+ * shapes beyond the rounding order of sums.
+ * x: DEVICE pointer, one right-hand side (complex64, n_s values).
+ * cache_path (may be NULL): a JSON-lines file.  A line whose "key" equals
+ * this plan's shape key (device name, SM count, order, depth, per level the
+ * grid, direction slots and operator list length, leaf count and sizes) is
+ * applied without timing; otherwise the result is appended as one line.
+ * out (may be NULL) receives the choice.  Synchronises the stream.
+ * Errors: INVALID_ARG (NULL plan or x, an FP64 plan, cache_path not
+ * writable, a cache line that does not parse), CUDA, OOM, TIMEOUT. */
+dfdm_status dfdm_plan_autotune(dfdm_plan plan, const void *x,
+                               const char *cache_path, void *stream,
+                               dfdm_tuning *out);
+
 /* Exports one level of one tree for bit-exact comparison with Alg. 1:
  * which = 0 targets, 1 sources; 0 <= level <= depth.  With keys == NULL only
  * *nboxes is set.  Otherwise keys/begin/end must hold *nboxes entries: the

@@ -25,7 +25,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_params_default", "dfdm_plan_create", "dfdm_apply", "dfdm_apply_host",
     "dfdm_plan_check", "dfdm_plan_stats", "dfdm_plan_export_tree",
     "dfdm_plan_export_offsets", "dfdm_plan_destroy", "dfdm_last_error", "dfdm_version",
-    "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_direct_rows", "dfdm_direct_rows_noalloc",
+    "dfdm_plan_set_timing", "dfdm_plan_timing", "dfdm_plan_autotune", "dfdm_direct_rows", "dfdm_direct_rows_noalloc",
     "dfdm_batch_create", "dfdm_batch_apply", "dfdm_batch_check", "dfdm_batch_plan",
     "dfdm_batch_info", "dfdm_batch_destroy",
     "dfdm_selector_param_count", "dfdm_selector_features", "dfdm_selector_forward",
@@ -70,6 +70,12 @@ class Timing(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("m2l_ms", ctypes.c_double * 16), ("launches", ctypes.c_int64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("m2l_nsplit", ctypes.c_int * 16), ("p2p_threads", ctypes.c_int), ("p2p_chunks", ctypes.c_int),
+                ("rule_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double), ("products", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -96,6 +102,7 @@ def load_library():
         "dfdm_direct_rows": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_direct_rows_noalloc": [vp, i64, vp, i64, dbl, vp, vp, i64, vp, vp],
         "dfdm_plan_timing": [vp, ctypes.POINTER(Timing)],
+        "dfdm_plan_autotune": [vp, vp, ctypes.c_char_p, vp, ctypes.POINTER(Tuning)],
         "dfdm_batch_create": [i32, ctypes.POINTER(Problem), ctypes.POINTER(Params), i32, vp,
                               ctypes.POINTER(vp)],
         "dfdm_batch_apply": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp],
@@ -299,6 +306,25 @@ class Plan:
 
     def check(self, stream=None):
         _check(self._lib.dfdm_plan_check(self._h, _stream_handle(stream)))
+
+    def autotune(self, x, cache=None, stream=None):
+        """Time candidate launch shapes (M2L chunks per level, nearfield
+        blocks) on products of x (one CUDA complex64 right-hand side) and
+        keep the fastest (dfdm_plan_autotune); cache: JSON-lines file path or
+        None.  Returns the choice as a dict."""
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.complex64):
+            raise TypeError("x must be a CUDA complex64 tensor")
+        x = x.contiguous()
+        if x.dim() != 1 or x.shape[0] != self.n_sources:
+            raise ValueError("x must hold one right-hand side of %d entries" % self.n_sources)
+        t = Tuning()
+        _check(self._lib.dfdm_plan_autotune(self._h, ctypes.c_void_p(x.data_ptr()),
+                                            None if cache is None else os.fsencode(cache),
+                                            _stream_handle(stream), ctypes.byref(t)))
+        return {"m2l_nsplit": list(t.m2l_nsplit), "p2p_threads": t.p2p_threads, "p2p_chunks": t.p2p_chunks,
+                "rule_ms": t.rule_ms, "tuned_ms": t.tuned_ms, "products": t.products,
+                "from_cache": bool(t.from_cache)}
 
     # ------------------------------------------------------------ queries
     def stats(self):

@@ -255,6 +255,17 @@ dfdm_status dfdm_plan_set_timing(dfdm_plan plan, int enable) {
   return DFDM_OK;
 }
 
+dfdm_status dfdm_plan_autotune(dfdm_plan plan, const void *x, const char *cache_path, void *stream,
+                               dfdm_tuning *out) {
+  if (!plan || !x) return fail(DFDM_ERR_INVALID_ARG, "NULL argument");
+  if (plan->p.params.precision != DFDM_TC_FP16X3)
+    return fail(DFDM_ERR_INVALID_ARG, "autotune applies to the tensor-core form only");
+  return guarded([&]() -> dfdm_status {
+    autotune_tc(plan->p, static_cast<const float2 *>(x), cache_path, static_cast<cudaStream_t>(stream), out);
+    return DFDM_OK;
+  });
+}
+
 dfdm_status dfdm_plan_timing(dfdm_plan plan, dfdm_timing *t) {
   if (!plan || !t) return fail(DFDM_ERR_INVALID_ARG, "NULL argument");
   Timing &tm = plan->p.timing;

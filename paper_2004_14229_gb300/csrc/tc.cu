@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "sm100_ptx.cuh"
@@ -1060,12 +1061,26 @@ __global__ void __launch_bounds__(256) k_l2t_small(const double *xyz, int64_t n_
 }
 
 // ----------------------------------------------------- nearfield (FP32)
-// One block per target leaf.  Each thread owns up to kP2pT targets of the
-// leaf (strided by the block size); the source points of every nearfield
-// leaf are staged through shared memory in chunks of 128.  Positions are
-// leaf-local FP32 (m_t - m_s = w d is exact), so |x - y| keeps FP32 relative
-// accuracy.  Each chunk's sum is formed in FP32 and added to an FP64 total,
-// so long source lists (512-point leaves) do not accumulate FP32 rounding.
+// exp(i 2 pi t) for t = kappa r / (2 pi) >= 0.  t is reduced to f = t - rint(t)
+// in [-1/2, 1/2]: adding and removing 1.5 * 2^23 rounds to the nearest integer
+// for t < 2^22, and t - rint(t) is exact (Sterbenz).  The hardware sine and
+// cosine then take 2 pi f in [-pi, pi], where CUDA documents their absolute
+// error as below 2^-21.4 (sine) and 2^-21.1 (cosine).
+__device__ __forceinline__ void exp_i_rev(float t, float &sn, float &cs) {
+  const float n = __fadd_rn(__fadd_rn(t, 12582912.f), -12582912.f);
+  __sincosf(6.28318530717958647692f * (t - n), &sn, &cs);
+}
+
+// Blocks (target leaf, target chunk): blockIdx.y of gridDim.y chunks of
+// kP2pT x blockDim.x targets of the leaf (a leaf of 512 points gives 128-thread
+// blocks one chunk, 32-thread blocks four, so that few large leaves still
+// fill the SMs).  Each thread owns up to kP2pT targets of its chunk (strided
+// by the block size); the source points of every nearfield leaf are staged
+// through shared memory, blockDim.x at a time.  Positions are leaf-local FP32
+// (m_t - m_s = w d is exact), so |x - y| keeps FP32 relative accuracy.  Every
+// 128 sources the FP32 partial sums are added to FP64 totals, so long source
+// lists (512-point leaves) do not accumulate FP32 rounding.  blockDim.x
+// divides 128.
 constexpr int kP2pT = 4;
 
 __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
@@ -1082,8 +1097,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
-  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
-  for (int p0 = b; p0 < e; p0 += kP2pT * blockDim.x) {
+  const float kap_rev = (float)((double)kappa / (2.0 * kPi));   // kappa r in revolutions
+  for (int p0 = b + blockIdx.y * kP2pT * blockDim.x; p0 < e; p0 += gridDim.y * kP2pT * blockDim.x) {
     float px[kP2pT], py[kP2pT], pz[kP2pT];
     double ar[kP2pT], ai[kP2pT];
     bool act[kP2pT];
@@ -1104,6 +1119,9 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
       const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
       if (s < 0) continue;
       const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
+      float cr[kP2pT], ci[kP2pT];
+#pragma unroll
+      for (int u = 0; u < kP2pT; ++u) cr[u] = ci[u] = 0.f;
       for (int q0 = sb[s]; q0 < se[s]; q0 += blockDim.x) {   // chunks of one source per thread
         const int cnt = min((int)blockDim.x, se[s] - q0);
         __syncthreads();
@@ -1117,9 +1135,6 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
         __syncthreads();
         // every staged source against the thread's kP2pT targets: independent
         // accumulation chains, one shared-memory read per source
-        float cr[kP2pT], ci[kP2pT];
-#pragma unroll
-        for (int u = 0; u < kP2pT; ++u) cr[u] = ci[u] = 0.f;
         for (int k = 0; k < cnt; ++k) {
           const float4 q = sp[k];
           const float2 v = sv[k];
@@ -1131,15 +1146,18 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
             // computed and never written
             const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
             float sn, cs;
-            sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+            exp_i_rev(kap_rev * (r2 * ir), sn, cs);   // exp(i kappa r)
             cr[u] = fmaf(ir, fmaf(cs, v.x, -sn * v.y), cr[u]);
             ci[u] = fmaf(ir, fmaf(cs, v.y, sn * v.x), ci[u]);
           }
         }
+        if (((q0 - sb[s]) & 127) + (int)blockDim.x >= 128 || q0 + (int)blockDim.x >= se[s]) {
 #pragma unroll
-        for (int u = 0; u < kP2pT; ++u) {
-          ar[u] += (double)cr[u];
-          ai[u] += (double)ci[u];
+          for (int u = 0; u < kP2pT; ++u) {
+            ar[u] += (double)cr[u];
+            ai[u] += (double)ci[u];
+            cr[u] = ci[u] = 0.f;
+          }
         }
       }
     }
@@ -1176,7 +1194,7 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
-  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
+  const float kap_rev = (float)((double)kappa / (2.0 * kPi));   // kappa r in revolutions
   for (int p0 = b; p0 < e; p0 += blockDim.x) {
     const int p = p0 + threadIdx.x;
     const bool act = p < e;
@@ -1217,7 +1235,7 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
             // coincident points (zero diagonal) add 0; idle threads are never written
             const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
             float sn, cs;
-            sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+            exp_i_rev(kap_rev * (r2 * ir), sn, cs);   // exp(i kappa r)
             const float fr = ir * cs, fi = ir * sn;
 #pragma unroll
             for (int r = 0; r < kP2pRG; ++r) {
@@ -1267,7 +1285,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, 
   const int b = leaf_begin[leaf];
   const int cnt = min(kSmallLeaf, leaf_end[leaf] - b);
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
-  const float kap_pi = (float)((double)kappa / kPi);   // exp(i kappa r) = cospi + i sinpi of kappa r / pi
+  const float kap_rev = (float)((double)kappa / (2.0 * kPi));   // kappa r in revolutions
   float px[kSmallLeaf], py[kSmallLeaf], pz[kSmallLeaf], cr[kSmallLeaf], ci[kSmallLeaf];
 #pragma unroll
   for (int u = 0; u < kSmallLeaf; ++u) {
@@ -1296,7 +1314,7 @@ __global__ void __launch_bounds__(256) k_p2p_small(const float *tl, int64_t nt, 
         if (r2 == 0.f) continue;   // coincident points (zero diagonal)
         const float ir = rsqrtf(r2);
         float sn, cs;
-        sincospif(kap_pi * (r2 * ir), &sn, &cs);   // exp(i kappa r)
+        exp_i_rev(kap_rev * (r2 * ir), sn, cs);   // exp(i kappa r)
         cr[u] = fmaf(ir, fmaf(cs, v.x, -sn * v.y), cr[u]);
         ci[u] = fmaf(ir, fmaf(cs, v.y, sn * v.x), ci[u]);
       }
@@ -1363,6 +1381,7 @@ struct TcState {
   float2 *ysorted = nullptr;
   int num_sms = 1;
   size_t l2_bytes = 0;
+  TcTuning tune;                         // launch shapes set by the tuner (0: the default rule)
 };
 
 // CTAs per (tile, alpha) for one M2L level.  Two reasons to split every
@@ -1391,6 +1410,25 @@ static int m2l_split(int units, int ops_per_alpha, int num_sms, size_t op_bytes,
   for (int s = s_min; s <= smax; ++s)
     if (cost(s) <= best * 1.02) return s;
   return s_min;
+}
+
+// CTA pairs of one M2L level: tiles of kPX x kPY x 2 kPZ parent cells.
+static int m2l_pairs(const LevelPlan &L) {
+  const int gp = L.grid / 2;
+  return ((gp + kPX - 1) / kPX) * ((gp + kPY - 1) / kPY) * ((gp + 2 * kPZ - 1) / (2 * kPZ));
+}
+
+static int m2l_ops_alpha(const LevelPlan &L) {
+  size_t ops_alpha = 0;
+  for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
+  return (int)ops_alpha;
+}
+
+// The default rule's chunk count of level l (m2l_split above).
+static int m2l_nsplit_rule(const Plan &plan, int l) {
+  const TcState &T = *plan.tc;
+  const LevelPlan &L = plan.levels[l];
+  return m2l_split(m2l_pairs(L), m2l_ops_alpha(L), T.num_sms / 2, (size_t)T.KP * T.KP * 4, T.l2_bytes);
 }
 
 static TcState &tc_state(Plan &plan) {
@@ -1594,6 +1632,16 @@ void build_tc(Plan &plan, cudaStream_t st) {
 
 // One right-hand side: far field into ys (sorted target order), then, when
 // `near` is set, the nearfield and the output y in the caller's order.
+// Default block shape of k_p2p_f32 (threads, target chunks per leaf).
+static void p2p_shape_rule(const Plan &plan, unsigned &threads, unsigned &chunks) {
+  const Tree &tt = plan.tt;
+  threads = (tt.n <= 64 * tt.nleaves) ? 32u : 128u;
+  const int64_t per128 = (tt.max_leaf_size + kP2pT * 128 - 1) / (kP2pT * 128);
+  if (threads == 128u && tt.nleaves * per128 * 4 < 16ll * plan.tc->num_sms) threads = 32u;
+  chunks = (unsigned)std::min<int64_t>(
+      16, std::max<int64_t>(1, (tt.max_leaf_size + kP2pT * threads - 1) / (kP2pT * threads)));
+}
+
 template <int O, int NP>
 static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, float2 *ys, bool near, cudaStream_t st) {
   constexpr int N = O * O * O;
@@ -1665,11 +1713,9 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, float2 *ys, bool 
       a.mom_exp = T.mom_exp + l;
       a.op_exp = T.op_exp[l];
       a.err = plan.err_flag;
-      const int gp = L.grid / 2;
-      const int pairs = ((gp + kPX - 1) / kPX) * ((gp + kPY - 1) / kPY) * ((gp + 2 * kPZ - 1) / (2 * kPZ));
-      size_t ops_alpha = 0;
-      for (int al = 0; al < 8; ++al) ops_alpha = std::max(ops_alpha, L.alpha_ops[al].size());
-      a.nsplit = m2l_split(pairs, (int)ops_alpha, T.num_sms / 2, (size_t)KP * KP * 4, T.l2_bytes);
+      const int pairs = m2l_pairs(L);
+      a.nsplit = (l < (int)T.tune.m2l_nsplit.size() && T.tune.m2l_nsplit[l] > 0) ? T.tune.m2l_nsplit[l]
+                                                                                 : m2l_nsplit_rule(plan, l);
       const int smem = PairSmem<NP>::kTotal;
       PhaseScope sc(tm, kPhM2L0 + l, st);
       k_m2l_pair<NP><<<dim3(2 * pairs, 8, a.nsplit), kPThreads, smem, st>>>(T.map_mhi[l], T.map_mlo[l], T.map_op, a);
@@ -1716,16 +1762,77 @@ static void apply_tc_o(Plan &plan, const float2 *x, float2 *y, float2 *ys, bool 
         ts.leaf_of_cell, ts.leaf_begin, ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
         (int)(plan.near_off.size() / 3), (float)plan.kappa, x, ys, y);
   } else {
-    // one block per target leaf; leaves of a few dozen points (uniform trees
-    // just above the warp-per-leaf size) get one warp, large ones 4 warps
-    const unsigned p2p_threads = (tt.n <= 64 * tt.nleaves) ? 32u : 128u;
-    k_p2p_f32<<<(unsigned)tt.nleaves, p2p_threads, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
+    // blocks (target leaf, target chunk): leaves of a few dozen points
+    // (uniform trees just above the warp-per-leaf size) get one warp; large
+    // leaves 4 warps, or one warp per chunk of kP2pT x 32 targets when one
+    // block per leaf would not give every SM about 16 warps
+    unsigned p2p_threads, chunks;
+    p2p_shape_rule(plan, p2p_threads, chunks);
+    if (T.tune.p2p_threads > 0) {
+      p2p_threads = (unsigned)T.tune.p2p_threads;
+      chunks = (unsigned)T.tune.p2p_chunks;
+    }
+    k_p2p_f32<<<dim3((unsigned)tt.nleaves, chunks), p2p_threads, 0, st>>>(T.tl, tt.n, tt.perm, tt.leaf_cell, tt.leaf_begin, tt.leaf_end,
                                                     T.sl, ts.n, ts.perm, ts.leaf_of_cell, ts.leaf_begin,
                                                     ts.leaf_end, 1 << p, (float)plan.levels[p].w, plan.near_off_dev,
                                                     (int)(plan.near_off.size() / 3), (float)plan.kappa, x,
                                                     ys, y);
   }
   DFDM_COUNT_LAUNCH(plan);
+}
+
+std::vector<int> tc_nsplit_candidates(const Plan &plan, int l) {
+  std::vector<int> c;
+  const LevelPlan &L = plan.levels[l];
+  if (l < std::max(1, plan.min_level) || l > plan.depth || L.off.empty()) return c;
+  const int rule = m2l_nsplit_rule(plan, l);
+  // at least one operator per chunk of every non-empty parity class
+  size_t ops_min = SIZE_MAX;
+  for (int al = 0; al < 8; ++al)
+    if (!L.alpha_ops[al].empty()) ops_min = std::min(ops_min, L.alpha_ops[al].size());
+  const int smax = std::max(rule, (int)std::min<size_t>(32, ops_min));
+  for (int s : {rule, rule / 2, rule * 2, rule - 1, rule + 1, 1, 4 * rule})
+    if (s >= 1 && s <= smax && std::find(c.begin(), c.end(), s) == c.end()) c.push_back(s);
+  return c;
+}
+
+std::vector<std::pair<int, int>> tc_p2p_candidates(const Plan &plan) {
+  std::vector<std::pair<int, int>> c;
+  const Tree &tt = plan.tt;
+  if (tt.nleaves == 0 || tt.max_leaf_size <= kSmallLeaf) return c;
+  unsigned t0, c0;
+  p2p_shape_rule(plan, t0, c0);
+  c.emplace_back((int)t0, (int)c0);
+  for (int t : {32, 64, 128})
+    for (int f : {1, 2}) {
+      const int ch = (int)std::min<int64_t>(16, f * std::max<int64_t>(1, (tt.max_leaf_size + kP2pT * t - 1) /
+                                                                             (kP2pT * t)));
+      if (std::find(c.begin(), c.end(), std::make_pair(t, ch)) == c.end()) c.emplace_back(t, ch);
+    }
+  return c;
+}
+
+TcTuning &tc_tuning(Plan &plan) { return plan.tc->tune; }
+
+std::string tc_shape_key(const Plan &plan) {
+  const TcState &T = *plan.tc;
+  int dev = 0;
+  cudaDeviceProp prop;
+  DFDM_CUDA_TRY(cudaGetDevice(&dev));
+  DFDM_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+  std::string k = std::string(prop.name) + "/sm" + std::to_string(T.num_sms) + "/o" + std::to_string(plan.order) +
+                  "/d" + std::to_string(plan.depth);
+  for (int l = std::max(1, plan.min_level); l <= plan.depth; ++l) {
+    const LevelPlan &L = plan.levels[l];
+    if (L.off.empty()) continue;
+    k += "/L" + std::to_string(l) + ":" + std::to_string(L.grid) + "," + std::to_string(L.slot_dir.size()) + "," +
+         std::to_string(m2l_ops_alpha(L));
+  }
+  k += "/leaf" + std::to_string(plan.tt.nleaves) + "," + std::to_string(plan.tt.max_leaf_size) + "," +
+       std::to_string(plan.tt.n);
+  for (char &ch : k)
+    if (ch == '"' || ch == '\\') ch = '_';
+  return k;
 }
 
 void apply_tc(Plan &plan, const float2 *x, float2 *y, int nrhs, cudaStream_t st) {

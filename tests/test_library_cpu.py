@@ -63,6 +63,7 @@ def test_invalid_arguments_return_status(lib):
     assert e.value.status == 6
     assert lib.dfdm_plan_destroy(None) == 0
     assert lib.dfdm_apply(None, None, None, 1, None) == 1
+    assert lib.dfdm_plan_autotune(None, None, None, None, None) == 1
 
 
 def test_plan_without_gpu_fails_cleanly(lib):

@@ -138,14 +138,14 @@ def _traffic(workload_name):
     ncu summary under profiles/ for this workload -- None when there is none
     or when csrc/tc.cu changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "m2l_tc_%s_dram.txt" % workload_name)
+    path = os.path.join(ROOT, "profiles", "m2l_pair_%s_dram.md" % workload_name)
     if not os.path.exists(path):
         return None
     fields = {}
     for line in open(path):
-        if ":" in line and not line.startswith(" "):
-            k, v = line.split(":", 1)
-            fields[k.strip()] = v.strip()
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
     src = os.path.join(ROOT, "paper_2004_14229_gb300", "csrc", "tc.cu")
     sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     if fields.get("tc.cu sha1") != sha or "dram bytes per product" not in fields:
@@ -658,7 +658,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="products timed end to end through dfdm_apply_host (0: none)")
     ap.add_argument("--batch", type=int, default=0, help="time the batched form on this many problems")
-    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=False,
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="time candidate launch shapes before the timed region and keep the fastest")
     ap.add_argument("--tune-cache", default=None, help="JSON-lines cache of the launch-shape tuner")
     ap.add_argument("--selector-study", action="store_true",

@@ -1083,6 +1083,61 @@ __device__ __forceinline__ void exp_i_rev(float t, float &sn, float &cs) {
 // divides 128.
 constexpr int kP2pT = 4;
 
+// Staged sources (k, k + 1) for k = 0, 2, .. < cnt2 against the thread's
+// kP2pT targets, two sources per packed FP32 instruction: adds
+// x_y exp(i kappa r) / (4 pi r) into the packed sums (even, odd source)
+// cr / ci.  Per pair: the differences, r^2, 1 / r (hardware rsqrt), kappa r
+// in revolutions t = kap_rev r, its exact reduction f = t - rint(t) (adding and
+// removing 1.5 * 2^23 rounds to the nearest integer for t < 2^22; t - rint(t)
+// is exact), the hardware sine and cosine of 2 pi f in [-pi, pi], and the
+// complex multiply-add.  SELF (the target's own leaf): coincident points
+// (the zero diagonal) add 0.  Other leaves hold no point equal to the target
+// (equal coordinates share a leaf); there r^2 gets 2^-100 added, which
+// leaves every representable distance unchanged and keeps 1 / r finite for
+// two distinct points that round to the same FP32 coordinates.
+template <bool SELF>
+__device__ __forceinline__ void p2p_staged(const float *qx, const float *qy, const float *qz, const float *vx,
+                                           const float *vy, const float *nvy, int cnt2,
+                                           const uint64_t (&PX)[kP2pT], const uint64_t (&PY)[kP2pT],
+                                           const uint64_t (&PZ)[kP2pT], uint64_t (&CR)[kP2pT],
+                                           uint64_t (&CI)[kP2pT], uint64_t KAP) {
+  const uint64_t MAG = ptx::f2_pack(12582912.f, 12582912.f);
+  const uint64_t TWOPI = ptx::f2_pack(6.28318530717958647692f, 6.28318530717958647692f);
+  const uint64_t TINY = ptx::f2_pack(0x1p-100f, 0x1p-100f);
+  for (int k = 0; k < cnt2; k += 2) {
+    const uint64_t QX = *reinterpret_cast<const uint64_t *>(qx + k);
+    const uint64_t QY = *reinterpret_cast<const uint64_t *>(qy + k);
+    const uint64_t QZ = *reinterpret_cast<const uint64_t *>(qz + k);
+    const uint64_t VX = *reinterpret_cast<const uint64_t *>(vx + k);
+    const uint64_t VY = *reinterpret_cast<const uint64_t *>(vy + k);
+    const uint64_t NVY = *reinterpret_cast<const uint64_t *>(nvy + k);
+#pragma unroll
+    for (int u = 0; u < kP2pT; ++u) {
+      const uint64_t D0 = ptx::f2_sub(PX[u], QX), D1 = ptx::f2_sub(PY[u], QY), D2 = ptx::f2_sub(PZ[u], QZ);
+      uint64_t R2 = ptx::f2_fma(D0, D0, ptx::f2_fma(D1, D1, ptx::f2_mul(D2, D2)));
+      if (!SELF) R2 = ptx::f2_add(R2, TINY);
+      float r2a, r2b;
+      ptx::f2_unpack(R2, r2a, r2b);
+      float ira = ptx::rsqrt_approx(r2a), irb = ptx::rsqrt_approx(r2b);
+      if (SELF) {
+        ira = r2a > 0.f ? ira : 0.f;
+        irb = r2b > 0.f ? irb : 0.f;
+      }
+      const uint64_t IR = ptx::f2_pack(ira, irb);
+      const uint64_t T = ptx::f2_mul(ptx::f2_mul(R2, IR), KAP);
+      const uint64_t N = ptx::f2_sub(ptx::f2_add(T, MAG), MAG);
+      const uint64_t TH = ptx::f2_mul(ptx::f2_sub(T, N), TWOPI);
+      float ta, tb, sa, ca, sb, cb;
+      ptx::f2_unpack(TH, ta, tb);
+      __sincosf(ta, &sa, &ca);
+      __sincosf(tb, &sb, &cb);
+      const uint64_t A = ptx::f2_mul(IR, ptx::f2_pack(ca, cb)), B = ptx::f2_mul(IR, ptx::f2_pack(sa, sb));
+      CR[u] = ptx::f2_fma(B, NVY, ptx::f2_fma(A, VX, CR[u]));
+      CI[u] = ptx::f2_fma(B, VX, ptx::f2_fma(A, VY, CI[u]));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
                                                  const int32_t *leaf_cell, const int32_t *leaf_begin,
                                                  const int32_t *leaf_end, const float *sl, int64_t ns,
@@ -1090,25 +1145,28 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
                                                  const int32_t *sb, const int32_t *se, int g, float w,
                                                  const int32_t *near_off, int nnear, float kappa,
                                                  const float2 *x, const float2 *ysorted, float2 *y) {
-  __shared__ float4 sp[128];
-  __shared__ float2 sv[128];
+  // staged sources, one array per component (pairs of consecutive sources
+  // are one 8-byte load); the odd slot after an odd count holds a zero value
+  __shared__ __align__(16) float qx[128], qy[128], qz[128], vx[128], vy[128], nvy[128];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
   const float kap_rev = (float)((double)kappa / (2.0 * kPi));   // kappa r in revolutions
+  const uint64_t KAP = ptx::f2_pack(kap_rev, kap_rev);
   for (int p0 = b + blockIdx.y * kP2pT * blockDim.x; p0 < e; p0 += gridDim.y * kP2pT * blockDim.x) {
-    float px[kP2pT], py[kP2pT], pz[kP2pT];
+    uint64_t PX[kP2pT], PY[kP2pT], PZ[kP2pT];
     double ar[kP2pT], ai[kP2pT];
     bool act[kP2pT];
 #pragma unroll
     for (int u = 0; u < kP2pT; ++u) {
       const int p = p0 + u * blockDim.x + threadIdx.x;
       act[u] = p < e;
-      px[u] = act[u] ? tl[p] : 0.f;
-      py[u] = act[u] ? tl[nt + p] : 0.f;
-      pz[u] = act[u] ? tl[2 * nt + p] : 0.f;
+      const float px = act[u] ? tl[p] : 0.f, py = act[u] ? tl[nt + p] : 0.f, pz = act[u] ? tl[2 * nt + p] : 0.f;
+      PX[u] = ptx::f2_pack(px, px);
+      PY[u] = ptx::f2_pack(py, py);
+      PZ[u] = ptx::f2_pack(pz, pz);
       ar[u] = 0.0;
       ai[u] = 0.0;
     }
@@ -1118,45 +1176,43 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
       if (sx < 0 || sy < 0 || sz < 0 || sx >= g || sy >= g || sz >= g) continue;
       const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
       if (s < 0) continue;
+      const bool self = (dx | dy | dz) == 0;
       const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
-      float cr[kP2pT], ci[kP2pT];
+      uint64_t CR[kP2pT], CI[kP2pT];
 #pragma unroll
-      for (int u = 0; u < kP2pT; ++u) cr[u] = ci[u] = 0.f;
+      for (int u = 0; u < kP2pT; ++u) CR[u] = CI[u] = 0ull;   // (+0, +0)
       for (int q0 = sb[s]; q0 < se[s]; q0 += blockDim.x) {   // chunks of one source per thread
         const int cnt = min((int)blockDim.x, se[s] - q0);
         __syncthreads();
         if (threadIdx.x < cnt) {
           const int q = q0 + threadIdx.x;
-          // source position relative to the target leaf's centre
-          sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
+          // source position relative to the target leaf's centre, x_y / (4 pi)
+          qx[threadIdx.x] = sl[q] - ox;
+          qy[threadIdx.x] = sl[ns + q] - oy;
+          qz[threadIdx.x] = sl[2 * ns + q] - oz;
           const float2 v = x[sperm[q]];
-          sv[threadIdx.x] = make_float2(v.x * inv4pi, v.y * inv4pi);   // x_y / (4 pi)
+          vx[threadIdx.x] = v.x * inv4pi;
+          vy[threadIdx.x] = v.y * inv4pi;
+          nvy[threadIdx.x] = -v.y * inv4pi;
+        } else if (threadIdx.x == cnt) {   // odd count: a source of value 0
+          qx[threadIdx.x] = qy[threadIdx.x] = qz[threadIdx.x] = 0.f;
+          vx[threadIdx.x] = vy[threadIdx.x] = nvy[threadIdx.x] = 0.f;
         }
         __syncthreads();
-        // every staged source against the thread's kP2pT targets: independent
-        // accumulation chains, one shared-memory read per source
-        for (int k = 0; k < cnt; ++k) {
-          const float4 q = sp[k];
-          const float2 v = sv[k];
-#pragma unroll
-          for (int u = 0; u < kP2pT; ++u) {
-            const float d0 = px[u] - q.x, d1 = py[u] - q.y, d2 = pz[u] - q.z;
-            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            // coincident points (zero diagonal) add 0; idle target slots are
-            // computed and never written
-            const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-            float sn, cs;
-            exp_i_rev(kap_rev * (r2 * ir), sn, cs);   // exp(i kappa r)
-            cr[u] = fmaf(ir, fmaf(cs, v.x, -sn * v.y), cr[u]);
-            ci[u] = fmaf(ir, fmaf(cs, v.y, sn * v.x), ci[u]);
-          }
-        }
+        const int cnt2 = (cnt + 1) & ~1;
+        if (self)
+          p2p_staged<true>(qx, qy, qz, vx, vy, nvy, cnt2, PX, PY, PZ, CR, CI, KAP);
+        else
+          p2p_staged<false>(qx, qy, qz, vx, vy, nvy, cnt2, PX, PY, PZ, CR, CI, KAP);
         if (((q0 - sb[s]) & 127) + (int)blockDim.x >= 128 || q0 + (int)blockDim.x >= se[s]) {
 #pragma unroll
           for (int u = 0; u < kP2pT; ++u) {
-            ar[u] += (double)cr[u];
-            ai[u] += (double)ci[u];
-            cr[u] = ci[u] = 0.f;
+            float r0, r1, i0, i1;
+            ptx::f2_unpack(CR[u], r0, r1);
+            ptx::f2_unpack(CI[u], i0, i1);
+            ar[u] += (double)r0 + (double)r1;
+            ai[u] += (double)i0 + (double)i1;
+            CR[u] = CI[u] = 0ull;
           }
         }
       }
@@ -1175,10 +1231,58 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
 // Nearfield for several right-hand sides (leaves above kSmallLeaf points):
 // one block per target leaf, one thread per target point (strided), and per
 // pass kP2pRG right-hand sides: each pair's kernel value f(x, y) is formed
-// once and multiplied into every right-hand side of the pass.  Sources
-// (positions and the pass's x values) are staged through shared memory in
-// chunks of the block size; chunk sums in FP32 are added into FP64.
+// once and multiplied into every right-hand side of the pass, two sources per
+// packed FP32 instruction.  Sources (positions and the pass's x values) are
+// staged through shared memory in chunks of the block size; chunk sums in
+// FP32 are added into FP64.
 constexpr int kP2pRG = 8;
+
+// Staged sources (k, k + 1), k = 0, 2, .. < cnt2, against the thread's
+// target for kP2pRG right-hand sides: the kernel value f(x, y) (same steps as
+// p2p_staged) is formed once per pair, two sources per packed instruction,
+// and multiplied into every right-hand side.  sv4[r][k / 2] holds
+// {vx_k, vx_k+1, vy_k, vy_k+1} of right-hand side r (x_y / (4 pi)).
+template <bool SELF>
+__device__ __forceinline__ void p2p_staged_mrhs(const float *qx, const float *qy, const float *qz,
+                                                const float4 (*sv4)[64], int cnt2, uint64_t PX, uint64_t PY,
+                                                uint64_t PZ, uint64_t (&CR)[kP2pRG], uint64_t (&CI)[kP2pRG],
+                                                uint64_t KAP) {
+  const uint64_t MAG = ptx::f2_pack(12582912.f, 12582912.f);
+  const uint64_t TWOPI = ptx::f2_pack(6.28318530717958647692f, 6.28318530717958647692f);
+  const uint64_t TINY = ptx::f2_pack(0x1p-100f, 0x1p-100f);
+  for (int k = 0; k < cnt2; k += 2) {
+    const uint64_t D0 = ptx::f2_sub(PX, *reinterpret_cast<const uint64_t *>(qx + k));
+    const uint64_t D1 = ptx::f2_sub(PY, *reinterpret_cast<const uint64_t *>(qy + k));
+    const uint64_t D2 = ptx::f2_sub(PZ, *reinterpret_cast<const uint64_t *>(qz + k));
+    uint64_t R2 = ptx::f2_fma(D0, D0, ptx::f2_fma(D1, D1, ptx::f2_mul(D2, D2)));
+    if (!SELF) R2 = ptx::f2_add(R2, TINY);
+    float r2a, r2b;
+    ptx::f2_unpack(R2, r2a, r2b);
+    float ira = ptx::rsqrt_approx(r2a), irb = ptx::rsqrt_approx(r2b);
+    if (SELF) {
+      ira = r2a > 0.f ? ira : 0.f;
+      irb = r2b > 0.f ? irb : 0.f;
+    }
+    const uint64_t IR = ptx::f2_pack(ira, irb);
+    const uint64_t T = ptx::f2_mul(ptx::f2_mul(R2, IR), KAP);
+    const uint64_t N = ptx::f2_sub(ptx::f2_add(T, MAG), MAG);
+    const uint64_t TH = ptx::f2_mul(ptx::f2_sub(T, N), TWOPI);
+    float ta, tb, sa, ca, sb, cb;
+    ptx::f2_unpack(TH, ta, tb);
+    __sincosf(ta, &sa, &ca);
+    __sincosf(tb, &sb, &cb);
+    const uint64_t FR = ptx::f2_mul(IR, ptx::f2_pack(ca, cb));
+    const uint64_t FI = ptx::f2_mul(IR, ptx::f2_pack(sa, sb));
+    const uint64_t NFI = ptx::f2_mul(IR, ptx::f2_pack(-sa, -sb));
+#pragma unroll
+    for (int r = 0; r < kP2pRG; ++r) {
+      const float4 v = sv4[r][k >> 1];
+      const uint64_t VX = ptx::f2_pack(v.x, v.y), VY = ptx::f2_pack(v.z, v.w);
+      CR[r] = ptx::f2_fma(FR, VX, ptx::f2_fma(NFI, VY, CR[r]));
+      CI[r] = ptx::f2_fma(FR, VY, ptx::f2_fma(FI, VX, CI[r]));
+    }
+  }
+}
 
 __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, const int32_t *tperm,
                                                   const int32_t *leaf_cell, const int32_t *leaf_begin,
@@ -1187,18 +1291,23 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
                                                   const int32_t *sb, const int32_t *se, int g, float w,
                                                   const int32_t *near_off, int nnear, float kappa, const float2 *x,
                                                   int nrhs, const float2 *ysorted, float2 *y) {
-  __shared__ float4 sp[128];
-  __shared__ float2 sv[kP2pRG][128];
+  __shared__ __align__(16) float qx[128], qy[128], qz[128];
+  __shared__ __align__(16) float4 sv4[kP2pRG][64];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
   const int b = leaf_begin[leaf], e = leaf_end[leaf];
   const float inv4pi = (float)(1.0 / (4.0 * kPi));
   const float kap_rev = (float)((double)kappa / (2.0 * kPi));   // kappa r in revolutions
+  const uint64_t KAP = ptx::f2_pack(kap_rev, kap_rev);
+  const int t = threadIdx.x;
+  // this thread's words of sv4: vx at (t / 2) * 4 + (t & 1), vy two further
+  const int wx = (t >> 1) * 4 + (t & 1);
   for (int p0 = b; p0 < e; p0 += blockDim.x) {
-    const int p = p0 + threadIdx.x;
+    const int p = p0 + t;
     const bool act = p < e;
     const float px = act ? tl[p] : 0.f, py = act ? tl[nt + p] : 0.f, pz = act ? tl[2 * nt + p] : 0.f;
+    const uint64_t PX = ptx::f2_pack(px, px), PY = ptx::f2_pack(py, py), PZ = ptx::f2_pack(pz, pz);
     for (int r0 = 0; r0 < nrhs; r0 += kP2pRG) {
       const int rn = min(kP2pRG, nrhs - r0);
       double ar[kP2pRG], ai[kP2pRG];
@@ -1210,44 +1319,48 @@ __global__ void __launch_bounds__(128) k_p2p_mrhs(const float *tl, int64_t nt, c
         if (sx < 0 || sy < 0 || sz < 0 || sx >= g || sy >= g || sz >= g) continue;
         const int s = s_leaf_of_cell[sx + g * (sy + g * sz)];
         if (s < 0) continue;
+        const bool self = (dx | dy | dz) == 0;
         const float ox = w * dx, oy = w * dy, oz = w * dz;   // m_t - m_s
         for (int q0 = sb[s]; q0 < se[s]; q0 += blockDim.x) {
           const int cnt = min((int)blockDim.x, se[s] - q0);
           __syncthreads();
-          if (threadIdx.x < cnt) {
-            const int q = q0 + threadIdx.x;
-            sp[threadIdx.x] = make_float4(sl[q] - ox, sl[ns + q] - oy, sl[2 * ns + q] - oz, 0.f);
+          if (t < cnt) {
+            const int q = q0 + t;
+            qx[t] = sl[q] - ox;
+            qy[t] = sl[ns + q] - oy;
+            qz[t] = sl[2 * ns + q] - oz;
             const int64_t src = sperm[q];
 #pragma unroll
             for (int r = 0; r < kP2pRG; ++r) {
               const float2 v = (r < rn) ? x[(int64_t)(r0 + r) * ns + src] : make_float2(0.f, 0.f);
-              sv[r][threadIdx.x] = make_float2(v.x * inv4pi, v.y * inv4pi);   // x_y / (4 pi)
+              float *sw = reinterpret_cast<float *>(sv4[r]);
+              sw[wx] = v.x * inv4pi;   // x_y / (4 pi)
+              sw[wx + 2] = v.y * inv4pi;
+            }
+          } else if (t == cnt) {   // odd count: a source of value 0
+            qx[t] = qy[t] = qz[t] = 0.f;
+#pragma unroll
+            for (int r = 0; r < kP2pRG; ++r) {
+              float *sw = reinterpret_cast<float *>(sv4[r]);
+              sw[wx] = sw[wx + 2] = 0.f;
             }
           }
           __syncthreads();
-          float cr[kP2pRG], ci[kP2pRG];
+          uint64_t CR[kP2pRG], CI[kP2pRG];
 #pragma unroll
-          for (int r = 0; r < kP2pRG; ++r) cr[r] = ci[r] = 0.f;
-          for (int k = 0; k < cnt; ++k) {
-            const float4 q = sp[k];
-            const float d0 = px - q.x, d1 = py - q.y, d2 = pz - q.z;
-            const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-            // coincident points (zero diagonal) add 0; idle threads are never written
-            const float ir = (r2 > 0.f) ? rsqrtf(r2) : 0.f;
-            float sn, cs;
-            exp_i_rev(kap_rev * (r2 * ir), sn, cs);   // exp(i kappa r)
-            const float fr = ir * cs, fi = ir * sn;
-#pragma unroll
-            for (int r = 0; r < kP2pRG; ++r) {
-              const float2 v = sv[r][k];
-              cr[r] = fmaf(fr, v.x, fmaf(-fi, v.y, cr[r]));
-              ci[r] = fmaf(fr, v.y, fmaf(fi, v.x, ci[r]));
-            }
-          }
+          for (int r = 0; r < kP2pRG; ++r) CR[r] = CI[r] = 0ull;
+          const int cnt2 = (cnt + 1) & ~1;
+          if (self)
+            p2p_staged_mrhs<true>(qx, qy, qz, sv4, cnt2, PX, PY, PZ, CR, CI, KAP);
+          else
+            p2p_staged_mrhs<false>(qx, qy, qz, sv4, cnt2, PX, PY, PZ, CR, CI, KAP);
 #pragma unroll
           for (int r = 0; r < kP2pRG; ++r) {
-            ar[r] += (double)cr[r];
-            ai[r] += (double)ci[r];
+            float r0v, r1v, i0v, i1v;
+            ptx::f2_unpack(CR[r], r0v, r1v);
+            ptx::f2_unpack(CI[r], i0v, i1v);
+            ar[r] += (double)r0v + (double)r1v;
+            ai[r] += (double)i0v + (double)i1v;
           }
         }
       }

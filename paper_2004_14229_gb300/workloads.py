@@ -39,6 +39,8 @@ WORKLOADS = {
     "uniform-256k-k64-d5-o6": dict(n=1 << 18, kappa=64.0, depth=5, order=6),
     "paper-grid-k6": dict(n=8 ** 6, kappa=6.4, depth=10, order=5, grid=6, n_max=512),
     "paper-grid-k7": dict(n=8 ** 7, kappa=12.8, depth=10, order=5, grid=7, n_max=512),
+    "paper-grid-k8": dict(n=8 ** 8, kappa=25.6, depth=10, order=5, grid=8, n_max=512),
+    "paper-grid-k9": dict(n=8 ** 9, kappa=51.2, depth=10, order=5, grid=9, n_max=512),
 }
 
 

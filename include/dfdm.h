@@ -138,22 +138,28 @@ dfdm_status dfdm_plan_check(dfdm_plan plan, void *stream);
 /* Copies the plan's counters into *st (host). */
 dfdm_status dfdm_plan_stats(dfdm_plan plan, dfdm_stats *st);
 
-/* Device time of the phases of Alg. 4 in the last dfdm_apply, per right-hand
- * side summed, from CUDA events recorded on the apply's stream (milliseconds).
- * m2l_ms[l] is the multiplication phase of level l; launches counts the
- * library's kernel launches of that apply. */
+/* Device time of the phases of Alg. 4, summed over the dfdm_apply calls made
+ * since timing was turned on or last read (and over their right-hand sides),
+ * from CUDA events recorded on each apply's stream (milliseconds).  m2l_ms[l]
+ * is the multiplication phase of level l; launches counts the library's kernel
+ * launches of those applies, applies the applies. */
 typedef struct {
   double s2m_ms, m2m_ms, split_ms, l2l_ms, l2t_ms, near_ms, total_ms;
   double m2l_ms[16];
   int64_t launches;
+  int64_t applies;
 } dfdm_timing;
 
-/* Turns per-phase event timing of later applies on (enable != 0) or off.
- * Timing adds event records to the stream but no synchronisation. */
+/* Turns per-phase event timing of later applies on (enable != 0) or off and
+ * drops any segments not yet read.  Timing adds event records to the stream
+ * but no synchronisation; the events of consecutive applies accumulate until
+ * dfdm_plan_timing reads them. */
 dfdm_status dfdm_plan_set_timing(dfdm_plan plan, int enable);
 
-/* Waits for the last timed apply's events and fills *t.  Returns
- * INVALID_ARG when timing is off or no apply ran since it was turned on. */
+/* Waits for the events of the applies since timing was turned on or last
+ * read, fills *t with their sums and starts a new accumulation.  Returns
+ * INVALID_ARG when timing is off or no apply ran since then.
+ * dfdm_plan_autotune drops segments not yet read. */
 dfdm_status dfdm_plan_timing(dfdm_plan plan, dfdm_timing *t);
 
 /* Launch shapes chosen by dfdm_plan_autotune and what they measured. */

@@ -67,7 +67,8 @@ class Problem(ctypes.Structure):
 class Timing(ctypes.Structure):
     _fields_ = [("s2m_ms", ctypes.c_double), ("m2m_ms", ctypes.c_double), ("split_ms", ctypes.c_double),
                 ("l2l_ms", ctypes.c_double), ("l2t_ms", ctypes.c_double), ("near_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("m2l_ms", ctypes.c_double * 16), ("launches", ctypes.c_int64)]
+                ("total_ms", ctypes.c_double), ("m2l_ms", ctypes.c_double * 16), ("launches", ctypes.c_int64),
+                ("applies", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -292,16 +293,19 @@ class Plan:
         return y
 
     def set_timing(self, enable=True):
-        """Record CUDA events around every phase of later applies."""
+        """Record CUDA events around every phase of later applies (no host
+        synchronisation; they accumulate until timing() reads them)."""
         _check(self._lib.dfdm_plan_set_timing(self._h, 1 if enable else 0))
 
     def timing(self):
-        """Per-phase device milliseconds of the last timed apply (dict)."""
+        """Per-phase device milliseconds summed over the applies since timing
+        was turned on or last read (dict; 'applies' counts them)."""
         t = Timing()
         _check(self._lib.dfdm_plan_timing(self._h, ctypes.byref(t)))
         out = {name: (list(getattr(t, name)) if name == "m2l_ms" else getattr(t, name))
                for name, _ in Timing._fields_}
         out["launches"] = int(out["launches"])
+        out["applies"] = int(out["applies"])
         return out
 
     def check(self, stream=None):

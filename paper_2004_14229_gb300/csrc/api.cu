@@ -228,7 +228,8 @@ dfdm_status dfdm_apply(dfdm_plan plan, const void *x, void *y, int nrhs, void *s
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> dfdm_status {
     Timing &tm = plan->p.timing;
-    tm.reset();
+    tm.launches = 0;
+    if (!tm.on) tm.reset();   // with timing on, segments accumulate until read
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (tm.on) {
       t0 = tm.next();
@@ -242,6 +243,8 @@ dfdm_status dfdm_apply(dfdm_plan plan, const void *x, void *y, int nrhs, void *s
       t1 = tm.next();
       DFDM_CUDA_TRY(cudaEventRecord(t1, st));
       tm.segs.push_back(Timing::Seg{-1, t0, t1});
+      tm.acc_launches += tm.launches;
+      ++tm.applies;
       tm.valid = true;
     }
     return DFDM_OK;
@@ -251,7 +254,7 @@ dfdm_status dfdm_apply(dfdm_plan plan, const void *x, void *y, int nrhs, void *s
 dfdm_status dfdm_plan_set_timing(dfdm_plan plan, int enable) {
   if (!plan) return fail(DFDM_ERR_INVALID_ARG, "NULL plan");
   plan->p.timing.on = enable != 0;
-  plan->p.timing.valid = false;
+  plan->p.timing.reset();
   return DFDM_OK;
 }
 
@@ -288,7 +291,9 @@ dfdm_status dfdm_plan_timing(dfdm_plan plan, dfdm_timing *t) {
           if (s.phase >= kPhM2L0 && s.phase < kPhM2L0 + 16) t->m2l_ms[s.phase - kPhM2L0] += ms;
       }
     }
-    t->launches = tm.launches;
+    t->launches = tm.acc_launches;
+    t->applies = tm.applies;
+    tm.reset();
     return DFDM_OK;
   });
 }

@@ -105,7 +105,9 @@ struct Timing {
     cudaEvent_t a, b;
   };
   std::vector<Seg> segs;
-  int64_t launches = 0;   // kernel launches of the last apply
+  int64_t launches = 0;       // kernel launches of the last apply
+  int64_t acc_launches = 0;   // launches of the applies since timing was turned on or read
+  int64_t applies = 0;        // applies whose segments are held
   cudaEvent_t next() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -117,7 +119,8 @@ struct Timing {
   void reset() {
     used = 0;
     segs.clear();
-    launches = 0;
+    acc_launches = 0;
+    applies = 0;
     valid = false;
   }
   void destroy() {

@@ -542,11 +542,13 @@ FP64_M2L_TFLOPS = 0.62        # measured rate of k_m2l_fp64 (4M workload, one pr
 def run_selector_study(args):
     """The learned selector against the fixed rule at 2^21 points.
 
-    Training: selector_problems(args.sel_train, kappa 2..96, depth 3), each
-    measured at orders 2..7 and two l_hf (selector_data.measure), problems
-    taken in order until args.sel_budget seconds are spent; samples at 57
-    tolerances 1e-1..1e-8 per level; full-batch Adam for 2000 epochs on the
-    GPU.  Fixed rule: per tolerance the smallest order whose error stays
+    Training (args.sel_recipe "mixed"): depth-3 problems (selector_problems,
+    kappa 2..96, orders 2..7) alternating with depth-4 problems of 8k-32k
+    points (kappa 8..300, tensor-core orders 2..6), problems without
+    admissible blocks skipped ("depth3": the depth-3 problems only, none
+    skipped); each measured at two l_hf (selector_data.measure), in order
+    until args.sel_budget seconds are spent; samples at 57 tolerances
+    1e-1..1e-8 per level; full-batch Adam for 2000 epochs on the GPU.  Fixed rule: per tolerance the smallest order whose error stays
     below tol / 3 on every training problem, with the default l_hf.  Test:
     2^21 uniform targets and sources (seeds 1, 2), depth 6, x seed 3, kappa in
     {32, 128, 256}, tol in {1e-3, 1e-5, 1e-7}; each choice is applied once
@@ -563,11 +565,38 @@ def run_selector_study(args):
 
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
+    if args.sel_recipe == "depth3":
+        queue = [(p, {}) for p in selector_problems(args.sel_train, seed0=200, kappa_range=(2.0, 96.0))]
+    else:
+        # depth-3 problems (orders 2..7) alternating with depth-4 problems of
+        # 8k-32k points up to kappa 300 (tensor-core orders 2..6), both only
+        # when they have admissible blocks
+        d3 = selector_problems(args.sel_train // 2, seed0=200, kappa_range=(2.0, 96.0))
+        d4 = selector_problems(args.sel_train - args.sel_train // 2, seed0=400, kappa_range=(8.0, 300.0),
+                               n_range=(1000, 4000), depths=(4,))
+        # van der Corput order, so that any prefix the time budget allows
+        # spans the whole kappa range
+        def spread(v):
+            def vdc(i):
+                x, f = 0.0, 0.5
+                while i:
+                    x += f * (i & 1)
+                    i >>= 1
+                    f /= 2
+                return x
+            return [v[i] for i in sorted(range(len(v)), key=vdc)]
+        d3, d4 = spread(d3), spread(d4)
+        queue = []
+        for i in range(max(len(d3), len(d4))):
+            if i < len(d3):
+                queue.append((d3[i], dict(require_far=True)))
+            if i < len(d4):
+                queue.append((d4[i], dict(orders=(2, 3, 4, 5, 6), tc_max=6, require_far=True)))
     train = []
-    for p in selector_problems(args.sel_train, seed0=200, kappa_range=(2.0, 96.0)):
+    for p, opt in queue:
         if time.perf_counter() - t0 > args.sel_budget:
             break
-        train += D.measure([p])
+        train += D.measure([p], **opt)
         print("measured %d problems, %.0f s" % (len(train), time.perf_counter() - t0), file=sys.stderr, flush=True)
     t_measure = time.perf_counter() - t0
     tols = np.logspace(-1, -8, 57)
@@ -576,7 +605,9 @@ def run_selector_study(args):
     fixed = {}
     for tol in SEL_TOLS:
         fixed[tol] = max(D.labels(r, tol)[0] for r in train)
-    print(json.dumps({"selector_training": {"problems": len(train), "samples": int(X.shape[0]),
+    print(json.dumps({"selector_training": {"recipe": args.sel_recipe, "problems": len(train),
+                                            "depths": sorted(set(r["depth"] for r in train)),
+                                            "samples": int(X.shape[0]),
                                             "measure_s": t_measure, "loss_first": float(losses[0]),
                                             "loss_last": float(losses[-1]),
                                             "fixed_rule_order": {str(k): v for k, v in fixed.items()}}}),
@@ -681,6 +712,8 @@ def main():
     ap.add_argument("--selector-study", action="store_true",
                     help="train the parameter selector and compare it with the fixed rule at 2^21 points")
     ap.add_argument("--sel-train", type=int, default=64, help="training problems of the selector study")
+    ap.add_argument("--sel-recipe", default="mixed", choices=["mixed", "depth3"],
+                    help="training problems: depth 3 and 4 with admissible blocks, or depth 3 only")
     ap.add_argument("--sel-budget", type=float, default=300.0,
                     help="seconds the selector study may spend measuring training problems")
     ap.add_argument("--sel-total", type=float, default=540.0,

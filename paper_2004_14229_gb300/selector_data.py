@@ -5,11 +5,12 @@ computed at Chebyshev orders 2..7, once with the default high-frequency level
 l_hf (Eq. 11's rule) and once with l_hf - 1, and compared with exact rows of
 Eq. (1) summed directly on the GPU (dfdm_direct_rows): the relative l2 error
 on sampled rows.  Orders up to 5 use the tensor-core form (their errors, above
-1e-5, are far above its ~1e-6 rounding), orders 6 and 7 the FP64 form.  For a
-tolerance tol, the label of every level l of the problem is
+1e-5, are far above its ~1e-6 rounding), orders 6 and 7 the FP64 form (or, for
+problems measured with the tensor-core form only, orders 2..6 in that form).
+For a tolerance tol, the label of every level l of the problem is
   * order: the smallest measured order whose error (default l_hf) is <= tol / 3
-    (a safety factor, so that the network's picks meet tol; 8 when none is),
-    scaled to (order - 2) / 8;
+    (a safety factor, so that the network's picks meet tol; one above the
+    highest measured order when none is), scaled to (order - 2) / 8;
   * direction flag: 1 when l <= l_hf_needed, where l_hf_needed = l_hf - 1 if
     that coarser choice still meets tol / 3 at the chosen order, else l_hf;
 and its features are dfdm_selector_features(kappa, root side, l, N, tol).
@@ -38,9 +39,9 @@ class _Reference:
         self.ref = direct_rows(torch.from_numpy(p["targets"]).cuda(), torch.from_numpy(p["sources"]).cuda(),
                                p["kappa"], self.x64, torch.from_numpy(self.rows).cuda()).cpu().numpy()
 
-    def error(self, order, l_hf):
+    def error(self, order, l_hf, tc_max=5):
         p = self.p
-        prec = TC_FP16X3 if order <= 5 else FP64
+        prec = TC_FP16X3 if order <= tc_max else FP64
         with Plan(p["targets"], p["sources"], p["kappa"], order=order, max_depth=p["max_depth"], l_hf=l_hf,
                   precision=prec) as pl:
             y = pl.apply(self.x32 if prec == TC_FP16X3 else self.x64).cpu().numpy()[self.rows]
@@ -59,11 +60,23 @@ def evaluate(p, order, l_hf, nrows=64, seed=13):
     return _Reference(p, nrows, seed).error(min(max(order, 2), ORDERS[-1]), l_hf)
 
 
-def measure(problems, orders=ORDERS, nrows=64, seed=13):
-    """One record per problem: kappa, N, depth, root side, default l_hf and
-    the error of every (order, l_hf shift) in {0, -1}."""
+def far_field_blocks(p):
+    """N_C of problem p's plan (0: every pair is nearfield, the product is
+    exact at any order)."""
+    with Plan(p["targets"], p["sources"], p["kappa"], order=2, max_depth=p["max_depth"], precision=FP64) as probe:
+        return probe.stats()["n_coupling"]
+
+
+def measure(problems, orders=ORDERS, nrows=64, seed=13, tc_max=5, require_far=False):
+    """One record per problem: kappa, N, depth, root side, default l_hf, the
+    measured orders and the error of every (order, l_hf shift) in {0, -1}.
+    Orders up to tc_max use the tensor-core form, higher ones FP64.
+    require_far: skip problems without admissible blocks (their error says
+    nothing about the interpolation order)."""
     recs = []
     for p in problems:
+        if require_far and far_field_blocks(p) == 0:
+            continue
         ref = _Reference(p, nrows, seed)
         lhf0 = default_l_hf(p)
         err = {}
@@ -72,9 +85,9 @@ def measure(problems, orders=ORDERS, nrows=64, seed=13):
             if lhf < -1 or (shift < 0 and lhf0 < 0):
                 continue
             for o in orders:
-                err[(o, shift)] = ref.error(o, lhf)
+                err[(o, shift)] = ref.error(o, lhf, tc_max)
         recs.append(dict(kappa=p["kappa"], n=p["targets"].shape[0], depth=p["max_depth"], root_side=1.0,
-                         l_hf=lhf0, err=err))
+                         l_hf=lhf0, err=err, orders=tuple(orders)))
     return recs
 
 
@@ -82,7 +95,10 @@ SAFETY = 3.0   # labels ask for an error of tol / SAFETY: the network's picks th
 
 
 def labels(rec, tol, orders=ORDERS, safety=SAFETY):
-    """(order needed, l_hf needed) of one record at tolerance tol."""
+    """(order needed, l_hf needed) of one record at tolerance tol (the
+    record's own measured orders when it lists them; one above the highest
+    when none suffices)."""
+    orders = rec.get("orders", orders)
     goal = tol / safety
     ok = [o for o in orders if rec["err"][(o, 0)] <= goal]
     o_need = min(ok) if ok else orders[-1] + 1

@@ -1138,7 +1138,7 @@ __device__ __forceinline__ void p2p_staged(const float *qx, const float *qy, con
   }
 }
 
-__global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
+__global__ void __launch_bounds__(128, 8) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
                                                  const int32_t *leaf_cell, const int32_t *leaf_begin,
                                                  const int32_t *leaf_end, const float *sl, int64_t ns,
                                                  const int32_t *sperm, const int32_t *s_leaf_of_cell,
@@ -1148,6 +1148,9 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
   // staged sources, one array per component (pairs of consecutive sources
   // are one 8-byte load); the odd slot after an odd count holds a zero value
   __shared__ __align__(16) float qx[128], qy[128], qz[128], vx[128], vy[128], nvy[128];
+  // FP64 totals of the thread's targets (shared memory keeps them out of the
+  // registers of the inner loop: 64 registers, eight blocks per SM)
+  __shared__ double acc_r[kP2pT][128], acc_i[kP2pT][128];
   const int leaf = blockIdx.x;
   const int cell = leaf_cell[leaf];
   const int cx = cell % g, cy = (cell / g) % g, cz = cell / (g * g);
@@ -1157,18 +1160,16 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
   const uint64_t KAP = ptx::f2_pack(kap_rev, kap_rev);
   for (int p0 = b + blockIdx.y * kP2pT * blockDim.x; p0 < e; p0 += gridDim.y * kP2pT * blockDim.x) {
     uint64_t PX[kP2pT], PY[kP2pT], PZ[kP2pT];
-    double ar[kP2pT], ai[kP2pT];
-    bool act[kP2pT];
 #pragma unroll
     for (int u = 0; u < kP2pT; ++u) {
       const int p = p0 + u * blockDim.x + threadIdx.x;
-      act[u] = p < e;
-      const float px = act[u] ? tl[p] : 0.f, py = act[u] ? tl[nt + p] : 0.f, pz = act[u] ? tl[2 * nt + p] : 0.f;
+      const bool act = p < e;
+      const float px = act ? tl[p] : 0.f, py = act ? tl[nt + p] : 0.f, pz = act ? tl[2 * nt + p] : 0.f;
       PX[u] = ptx::f2_pack(px, px);
       PY[u] = ptx::f2_pack(py, py);
       PZ[u] = ptx::f2_pack(pz, pz);
-      ar[u] = 0.0;
-      ai[u] = 0.0;
+      acc_r[u][threadIdx.x] = 0.0;
+      acc_i[u][threadIdx.x] = 0.0;
     }
     for (int i = 0; i < nnear; ++i) {
       const int dx = near_off[3 * i], dy = near_off[3 * i + 1], dz = near_off[3 * i + 2];
@@ -1210,8 +1211,8 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
             float r0, r1, i0, i1;
             ptx::f2_unpack(CR[u], r0, r1);
             ptx::f2_unpack(CI[u], i0, i1);
-            ar[u] += (double)r0 + (double)r1;
-            ai[u] += (double)i0 + (double)i1;
+            acc_r[u][threadIdx.x] += (double)r0 + (double)r1;
+            acc_i[u][threadIdx.x] += (double)i0 + (double)i1;
             CR[u] = CI[u] = 0ull;
           }
         }
@@ -1220,9 +1221,10 @@ __global__ void __launch_bounds__(128) k_p2p_f32(const float *tl, int64_t nt, co
 #pragma unroll
     for (int u = 0; u < kP2pT; ++u) {
       const int p = p0 + u * blockDim.x + threadIdx.x;
-      if (act[u]) {
+      if (p < e) {
         const float2 f = ysorted[p];
-        y[tperm[p]] = make_float2((float)(ar[u] + (double)f.x), (float)(ai[u] + (double)f.y));
+        y[tperm[p]] = make_float2((float)(acc_r[u][threadIdx.x] + (double)f.x),
+                                  (float)(acc_i[u][threadIdx.x] + (double)f.y));
       }
     }
   }

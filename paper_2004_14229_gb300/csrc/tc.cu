@@ -4,32 +4,39 @@
 // admissible offsets d (Sect. 2.6, multiplication phase; one stored operator
 // per level and offset, Sect. 2.7), runs on the tcgen05 tensor cores
 // (k_m2l_pair):
-//   * complex n x n products are real-stacked: outputs [Re; Im] (rows) times
+//   * complex n x n products are real-stacked: outputs [Re; Im] (N) times
 //     inputs [Re v; Im v] (K), each padded to NP = KP (a multiple of 64);
 //   * each value a is split into two FP16 terms a = a_hi + a_lo (a_hi =
 //     fp16(a), a_lo = fp16(a - a_hi)) after a power-of-two scale per level,
 //     and the product takes a_hi b_hi + a_lo b_hi + a_hi b_lo with FP32
 //     accumulation in TMEM (the dropped a_lo b_lo is ~2^-22 relative);
+//     H = M_hi O_hi lives for one unit of kPU stages (the accumulator is
+//     truncated toward zero after every instruction), X = M_lo O_hi +
+//     M_hi O_lo for kPXUnits units;
 //   * a cluster of two CTAs owns 256 targets of one parity alpha (an
 //     8 x 4 x 8 block of the parent grid) and walks one chunk of the level's
 //     offset list for alpha with tcgen05.mma.cta_group::2 (M = 256, every row
-//     a target; each CTA holds half of every operator tile); the source
-//     moments of a CTA's 128 targets for offset d are one TMA box with
-//     element stride 2 in x, y, z over the dense moment grid, so out-of-grid
-//     sources arrive as zeros; each CTA's share of an operator stage is one
-//     bulk copy of its pre-swizzled image;
-//   * warp roles: 0 copies (both CTAs), 1 issues MMAs (rank 0), 2 forwards
-//     rank 1's completed stages to rank 0 (rank 1), 4-11 drain TMEM into
-//     FP32 running sums held in registers and flush them into the FP64
-//     locals.  Every wait is bounded; a wait that gives up sets the plan's
-//     error word (read by dfdm_plan_check) and both CTAs leave their loops.
+//     a target; N = 224, one half of the stacked outputs per pass; each CTA
+//     holds half of every operator tile);
+//   * moments are split into a parity layout [slot][K step][parity][z/2]
+//     [y/2][x/2][32], so a CTA's 128 source rows for offset d are one 5-D TMA
+//     box (out-of-grid sources arrive as zeros); a CTA's share of an operator
+//     stage is one 2-D TMA box of its pre-swizzled image; both CTAs' copies
+//     complete on rank 0's per-unit "go" barrier (.cta_group::2);
+//   * warp roles: 0 copies (both CTAs), 1 issues the MMAs (rank 0) and owns
+//     TMEM (both), 2-13 drain H and X into FP32 running sums held in
+//     registers and add them to the FP64 locals by coalesced atomics, one
+//     32 x 16 slice every second unit.  Every wait is bounded; a wait that
+//     gives up sets the plan's error word (read by dfdm_plan_check) and both
+//     CTAs leave their loops.
 //
-// The other phases (S2M, M2M, L2L, L2T, nearfield) run in FP32 on the CUDA
-// cores with FP64 reduction of large phase arguments; moments are
+// S2M and L2T run in FP64 (coordinates, Lagrange basis, plane waves, sums);
+// M2M and L2L in FP32 with FP64 phase tables; the nearfield in FP32 on
+// packed pairs (two sources per instruction) with FP64 totals.  Moments are
 // real-stacked FP32 rows [Re 0..n-1 | Im 0..n-1 | pad] of KP floats, locals
 // FP64 rows [Re 0..n-1 | pad | Im 0..n-1 | pad] with the imaginary part at
-// KP / 2 (both halves start on 128-byte boundaries: the M2L adds them with
-// bulk reductions).
+// KP / 2 (both halves start on 128-byte boundaries for the coalesced
+// slice additions).
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
@@ -1071,17 +1078,7 @@ __device__ __forceinline__ void exp_i_rev(float t, float &sn, float &cs) {
   __sincosf(6.28318530717958647692f * (t - n), &sn, &cs);
 }
 
-// Blocks (target leaf, target chunk): blockIdx.y of gridDim.y chunks of
-// kP2pT x blockDim.x targets of the leaf (a leaf of 512 points gives 128-thread
-// blocks one chunk, 32-thread blocks four, so that few large leaves still
-// fill the SMs).  Each thread owns up to kP2pT targets of its chunk (strided
-// by the block size); the source points of every nearfield leaf are staged
-// through shared memory, blockDim.x at a time.  Positions are leaf-local FP32
-// (m_t - m_s = w d is exact), so |x - y| keeps FP32 relative accuracy.  Every
-// 128 sources the FP32 partial sums are added to FP64 totals, so long source
-// lists (512-point leaves) do not accumulate FP32 rounding.  blockDim.x
-// divides 128.
-constexpr int kP2pT = 4;
+constexpr int kP2pT = 4;   // targets per thread of k_p2p_f32
 
 // Staged sources (k, k + 1) for k = 0, 2, .. < cnt2 against the thread's
 // kP2pT targets, two sources per packed FP32 instruction: adds
@@ -1138,6 +1135,17 @@ __device__ __forceinline__ void p2p_staged(const float *qx, const float *qy, con
   }
 }
 
+// Nearfield, leaves above kSmallLeaf points.  Blocks (target leaf, target
+// chunk): blockIdx.y of gridDim.y chunks of kP2pT x blockDim.x targets of the
+// leaf (a leaf of 512 points gives 128-thread blocks one chunk, 32-thread
+// blocks four, so that few large leaves still fill the SMs).  Each thread
+// owns up to kP2pT targets of its chunk (strided by the block size); the
+// source points of every nearfield leaf are staged through shared memory,
+// blockDim.x at a time, and p2p_staged runs them against the thread's
+// targets.  Positions are leaf-local FP32 (m_t - m_s = w d is exact), so
+// |x - y| keeps FP32 relative accuracy.  Every 128 sources the FP32 partial
+// sums are added to FP64 totals, so long source lists (512-point leaves) do
+// not accumulate FP32 rounding.  blockDim.x divides 128.
 __global__ void __launch_bounds__(128, 8) k_p2p_f32(const float *tl, int64_t nt, const int32_t *tperm,
                                                  const int32_t *leaf_cell, const int32_t *leaf_begin,
                                                  const int32_t *leaf_end, const float *sl, int64_t ns,

@@ -133,11 +133,24 @@ def job_rate(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+def _m2l_source_sha1():
+    """sha1 of the M2L kernel's source: csrc/tc.cu from its "M2L (TC)"
+    section marker to the "L2T" one (arguments, shared-memory plan, operator
+    image writer, k_m2l_pair), plus the PTX helper header it uses."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2004_14229_gb300", "csrc")
+    text = open(os.path.join(csrc, "tc.cu")).read()
+    a = text.index("// ------------------------------------------------------------- M2L (TC)")
+    b = text.index("// ----------------------------------------------------------------- L2T")
+    h = hashlib.sha1(text[a:b].encode())
+    h.update(open(os.path.join(csrc, "sm100_ptx.cuh"), "rb").read())
+    return h.hexdigest()
+
+
 def _traffic(workload_name):
     """HBM bytes (read + write) of all M2L launches of one product, from the
     ncu summary under profiles/ for this workload -- None when there is none
-    or when csrc/tc.cu changed since the counters were taken."""
-    import hashlib
+    or when the M2L kernel's source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "m2l_pair_%s_dram.md" % workload_name)
     if not os.path.exists(path):
         return None
@@ -146,9 +159,7 @@ def _traffic(workload_name):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    src = os.path.join(ROOT, "paper_2004_14229_gb300", "csrc", "tc.cu")
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if fields.get("tc.cu sha1") != sha or "dram bytes per product" not in fields:
+    if fields.get("k_m2l_pair source sha1") != _m2l_source_sha1() or "dram bytes per product" not in fields:
         return None
     return float(fields["dram bytes per product"])
 

@@ -18,6 +18,8 @@ Matrix-Vector Multiplication".  The code follows the paper's order:
   Sect. 2.6, Alg. 4        the product g = A v              FDMOracle.apply()
   Sect. 2.7                8 reference E_{t'}, one A per    mode="reuse"
                            reference configuration
+  Sect. 2.7 (closing)      A ~ U V^* by partially pivoted   mode="aca"
+                           ACA (oracle/aca.py)
 
 Readings where the paper is silent or garbled:
   R1  Eq. (4) prints cos((2 nu - 1)/(2 pi (m+1))); the misplaced pi is read as
@@ -45,6 +47,8 @@ Readings where the paper is silent or garbled:
 import math
 
 import numpy as np
+
+from .aca import aca_partial
 
 FOUR_PI = 4.0 * math.pi
 
@@ -461,7 +465,7 @@ class FDMOracle:
         return lag * np.exp(1j * self.kappa * (pts @ cv))[:, None]
 
     # ----------------------------------------------------------------- Alg. 4
-    def apply(self, x, rows=None, mode="reuse"):
+    def apply(self, x, rows=None, mode="reuse", aca_tol=1e-8):
         """g = A v by Alg. 4.  Returns g at `rows` (all target rows when None).
 
         mode="literal": every L, E and A matrix is formed for its own block
@@ -470,10 +474,13 @@ class FDMOracle:
         level and box offset, each E_{t'} once per level and octant, and the
         diagonal directional part E^d is applied separately; the M2L updates
         that share a stored matrix are applied as one matrix product.
+        mode="aca": as "reuse", with every stored coupling matrix replaced by
+        its partially pivoted ACA U V^* to relative tolerance aca_tol (Sect.
+        2.7, closing remark); the ranks are left in self.last_aca_ranks.
         With rows given, only the blocks of Alg. 2 whose target box contains a
         requested row (or an ancestor of one) are formed and applied.
         """
-        if mode not in ("literal", "reuse"):
+        if mode not in ("literal", "reuse", "aca"):
             raise ValueError(mode)
         tt, ts, dirs = self.tt, self.ts, self.dirs
         kappa, n = self.kappa, self.n
@@ -538,6 +545,8 @@ class FDMOracle:
                     gt[(t, c)] += self.coupling_matrix(t, s, cv) @ vt[(s, c)]
         else:
             groups = {}
+            aca_ranks = {}
+            self.last_aca_ranks = aca_ranks
             for (t, s) in blocks.adm:
                 d = tt.ijk[t] - ts.ijk[s]
                 key = (tt.level[t], int(d[0]), int(d[1]), int(d[2]))
@@ -548,7 +557,12 @@ class FDMOracle:
                 cv = dirs.vector(tt.level[t0], c)
                 amat = self.coupling_matrix(t0, s0, cv)   # reference configuration
                 vin = np.stack([vt[(s, c)] for (_, s) in pairs], axis=1)
-                out = amat @ vin
+                if mode == "aca":
+                    u, w = aca_partial(amat, aca_tol)
+                    aca_ranks[key] = u.shape[1]
+                    out = u @ (w.conj().T @ vin)
+                else:
+                    out = amat @ vin
                 for i, (t, _) in enumerate(pairs):
                     gt[(t, c)] += out[:, i]
 

@@ -284,6 +284,19 @@ dfdm_status dfdm_uniform_counts(double kappa, double eta2, double root_side,
                                 int64_t *n_stored_coupling,
                                 int64_t *near_leaf_pairs);
 
+/* Partially pivoted adaptive cross approximation of one coupling matrix,
+ * A ~ U V^* (Sect. 2.7, closing remark; host only, a set-up step).  a: host,
+ * m x n complex128, row-major.  Step k takes the residual of one row, its
+ * largest entry as pivot column, and the residual of that column; the
+ * approximation stops once |u_k| |v_k| <= tol ||S_k||_F (S_k the current
+ * approximation, the k-th term kept; tol >= 0, 0 runs to max_rank) or at
+ * max_rank columns.  u: host m x max_rank complex128, v: host n x max_rank
+ * complex128, both row-major, column l holding u_l and v_l (a ~ u v^*);
+ * columns from *rank on are zero.  u and v may be NULL when max_rank is 0.
+ * Errors: INVALID_ARG, OOM. */
+dfdm_status dfdm_aca(const void *a, int m, int n, double tol, int max_rank,
+                     void *u, void *v, int *rank);
+
 /* The coupling structure of one level of such a uniform tree, in the format
  * of dfdm_plan_export_offsets (offsets d = t - s and direction indices for
  * targets of parity alpha_index), from the planner alone (host only).

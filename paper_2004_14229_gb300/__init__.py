@@ -29,7 +29,7 @@ EXPORTED_SYMBOLS = [
     "dfdm_batch_create", "dfdm_batch_apply", "dfdm_batch_check", "dfdm_batch_plan",
     "dfdm_batch_info", "dfdm_batch_destroy",
     "dfdm_selector_param_count", "dfdm_selector_features", "dfdm_selector_forward",
-    "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params", "dfdm_uniform_counts",
+    "dfdm_selector_grad", "dfdm_selector_train", "dfdm_select_params", "dfdm_aca", "dfdm_uniform_counts",
     "dfdm_uniform_offsets",
 ]
 
@@ -117,6 +117,7 @@ def load_library():
         "dfdm_selector_grad": [vp, vp, vp, i64, vp, vp, vp],
         "dfdm_selector_train": [vp, vp, vp, i64, i32, ctypes.c_float, vp, vp, vp],
         "dfdm_select_params": [vp, dbl, dbl, i64, ctypes.POINTER(Params), vp],
+        "dfdm_aca": [vp, i32, i32, dbl, i32, vp, vp, ctypes.POINTER(i32)],
         "dfdm_uniform_counts": [dbl, dbl, dbl, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                 ctypes.POINTER(i64)],
         "dfdm_uniform_offsets": [dbl, dbl, dbl, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), vp, vp],
@@ -148,6 +149,20 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def aca(a, tol, max_rank=None):
+    """Partially pivoted ACA a ~ U @ V.conj().T of a complex matrix (host
+    only, dfdm_aca; Sect. 2.7).  Returns (U (m x k), V (n x k))."""
+    lib = load_library()
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    m, n = a.shape
+    kmax = min(m, n) if max_rank is None else int(max_rank)
+    u = np.zeros((m, max(kmax, 1)), dtype=np.complex128)
+    v = np.zeros((n, max(kmax, 1)), dtype=np.complex128)
+    k = ctypes.c_int(0)
+    _check(lib.dfdm_aca(a.ctypes.data, m, n, float(tol), kmax, u.ctypes.data, v.ctypes.data, ctypes.byref(k)))
+    return u[:, :k.value].copy(), v[:, :k.value].copy()
 
 
 def uniform_counts(kappa, depth, eta2=5.0, root_side=1.0, l_hf=None):

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfdm.so")
-SOURCES = ["api.cu", "tree.cu", "planner.cu", "fp64.cu", "tc.cu", "direct.cu", "batch.cu", "selector.cu", "tune.cu"]
+SOURCES = ["api.cu", "tree.cu", "planner.cu", "fp64.cu", "tc.cu", "direct.cu", "batch.cu", "selector.cu", "tune.cu", "aca.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
          "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -63,7 +63,9 @@ def test_1m_fp64_and_tensor_core_forms():
 
 def test_4m_tensor_core_form_rows_against_oracle():
     """The benchmark workload (2^22 points, kappa 128, depth 7, order 6):
-    the tensor-core form within 1e-6 of 256 oracle rows."""
+    the tensor-core form within 1e-6 of 256 oracle rows, with the built-in
+    launch shapes and with the tuned ones bench.py times."""
+    import torch
     name = "uniform-4M-k128-d7-o6"
     g = _golden(name)
     plan, xin = _plan(name, pkg.TC_FP16X3)
@@ -71,4 +73,8 @@ def test_4m_tensor_core_form_rows_against_oracle():
         assert plan.stats()["l_hf"] == int(g["l_hf"])
         y = gpu_apply(plan, xin)
         plan.check()
+        plan.autotune(torch.from_numpy(xin).cuda())
+        y_tuned = gpu_apply(plan, xin)
+        plan.check()
     _check_rows(name + " TC", y, 1e-6, g)
+    _check_rows(name + " TC, tuned launch shapes", y_tuned, 1e-6, g)

@@ -550,6 +550,14 @@ SEL_N, SEL_DEPTH = 1 << 21, 6
 FP64_M2L_TFLOPS = 0.62        # measured rate of k_m2l_fp64 (4M workload, one product)
 
 
+def selector_record_json(rec):
+    """A measured selector record (selector_data.measure) as plain JSON."""
+    out = {k: v for k, v in rec.items() if k != "err"}
+    out["orders"] = list(rec.get("orders", ()))
+    out["err"] = [[int(o), int(sh), float(e)] for (o, sh), e in sorted(rec["err"].items())]
+    return out
+
+
 def run_selector_study(args):
     """The learned selector against the fixed rule at 2^21 points.
 
@@ -610,6 +618,10 @@ def run_selector_study(args):
         train += D.measure([p], **opt)
         print("measured %d problems, %.0f s" % (len(train), time.perf_counter() - t0), file=sys.stderr, flush=True)
     t_measure = time.perf_counter() - t0
+    if args.sel_save:
+        # the measured errors, for offline work on the network and its labels
+        with open(args.sel_save, "w") as f:
+            json.dump([selector_record_json(r) for r in train], f)
     tols = np.logspace(-1, -8, 57)
     X, T = D.make_samples(train, tols)
     sel, losses = pkg.Selector.train(selector_init(), X, T, epochs=2000, lr=3e-3)
@@ -729,6 +741,7 @@ def main():
                     help="seconds the selector study may spend measuring training problems")
     ap.add_argument("--sel-total", type=float, default=540.0,
                     help="no FP64 cell of the selector study starts after this many seconds")
+    ap.add_argument("--sel-save", default=None, help="write the measured training records to this JSON file")
     ap.add_argument("--sel-fp64-cap", type=float, default=110.0,
                     help="skip FP64 products of the selector study whose M2L is estimated above this (s)")
     args = ap.parse_args()

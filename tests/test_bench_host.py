@@ -81,3 +81,12 @@ def test_selector_samples_have_one_row_per_level_and_tolerance():
     assert X.shape == (2 * 2 + 2 * 3, 4) and T.shape == (10, 2)
     assert T[0, 0] == pytest.approx((4 - 2) / 8.0)             # first record, tol 1e-2
     assert T[-1, 0] == pytest.approx((7 - 2) / 8.0)            # second record: none suffices
+
+
+def test_selector_record_json_round_trip():
+    import json
+    r = _rec(ERRS, (2, 3, 4, 5, 6, 7), errs_m1=[1e-1, 3e-2, 2e-3, 5e-4, 6e-5, 7e-6])
+    j = json.loads(json.dumps(bench.selector_record_json(r)))
+    assert j["orders"] == [2, 3, 4, 5, 6, 7] and j["l_hf"] == 3
+    back = {(o, sh): e for o, sh, e in j["err"]}
+    assert back == r["err"]

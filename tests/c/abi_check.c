@@ -53,5 +53,36 @@ int main(void) {
             fabs(feat[0] - 0.2f) < 1e-6 && fabs(feat[2] - log2(1.0 + 64.0) / 16.0) < 1e-6 &&
             fabs(feat[3] - 0.4f) < 1e-6,
         "selector features");
+  {
+    /* the rank-1 4 x 3 complex matrix a[i][j] = ((i + 1) + i I) (j + 1), as interleaved
+       (re, im) doubles; its ACA reproduces it */
+    double a[24], u[24], v[18];
+    int rank = -1, i, j, l;
+    for (i = 0; i < 4; ++i)
+      for (j = 0; j < 3; ++j) {
+        a[2 * (3 * i + j)] = (double)((i + 1) * (j + 1));
+        a[2 * (3 * i + j) + 1] = (double)(i * (j + 1));
+      }
+    check(dfdm_aca(a, 4, 3, 1e-12, 3, u, v, &rank) == DFDM_OK && rank >= 1 && rank <= 2, "aca runs");
+    {
+      double err = 0.0, nrm = 0.0;
+      for (i = 0; i < 4; ++i)
+        for (j = 0; j < 3; ++j) {
+          double re = 0.0, im = 0.0; /* sum_l u[i][l] conj(v[j][l]) */
+          for (l = 0; l < 3; ++l) {
+            const double ur = u[2 * (3 * i + l)], ui = u[2 * (3 * i + l) + 1];
+            const double vr = v[2 * (3 * j + l)], vi = -v[2 * (3 * j + l) + 1];
+            re += ur * vr - ui * vi;
+            im += ur * vi + ui * vr;
+          }
+          err += (re - a[2 * (3 * i + j)]) * (re - a[2 * (3 * i + j)]) +
+                 (im - a[2 * (3 * i + j) + 1]) * (im - a[2 * (3 * i + j) + 1]);
+          nrm += a[2 * (3 * i + j)] * a[2 * (3 * i + j)] + a[2 * (3 * i + j) + 1] * a[2 * (3 * i + j) + 1];
+        }
+      check(sqrt(err) <= 1e-12 * sqrt(nrm), "aca reproduces a low-rank matrix");
+    }
+    check(dfdm_aca(NULL, 4, 3, 1e-12, 3, u, v, &rank) == DFDM_ERR_INVALID_ARG, "aca NULL matrix");
+    check(dfdm_plan_autotune(NULL, NULL, NULL, NULL, NULL) == DFDM_ERR_INVALID_ARG, "autotune NULL plan");
+  }
   return fails != 0;
 }
